@@ -1,0 +1,301 @@
+"""Benchmark: AIRG-preconditioned FGMRES (setup + solve to rtol 1e-8) on one GB300 per rank.
+
+A step is one pass of the whole path over one synthetic system: airg_setup (CF splitting, GMRES
+polynomials, restrictor, coarse matrices on every level), airg_solve to rtol 1e-8, airg_free.
+The workload is the 2D upwind P1 DG system on 1024 x 1024 jittered squares (6,291,456 DOFs,
+sigma piecewise constant on a seeded 8 x 8 block pattern with values {0, 1, 10}, theta = 0.3).
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent replica (a single
+system does not shard without a halo exchange); value = DOFs of all ranks / max time.
+
+--impl reference times the CPU oracle (plain single-thread FP64 restatement of the method) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AIRG-GMRES time-to-rtol 1e-8 (DOFs/s, HBM GB/s): mixed/batched vs FP64 on GB300"
+UNIT = "DOFs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="airg", choices=["airg", "reference"])
+    ap.add_argument("--mesh", type=int, default=1024)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-mesh", type=int, default=320)
+    return ap.parse_args()
+
+
+def workload_name(mesh: int) -> str:
+    return (f"2D upwind P1 DG, {mesh}x{mesh} jittered squares ({6 * mesh * mesh:,} DOFs), sigma on a seeded 8x8 "
+            f"block pattern from {{0,1,10}}, theta=0.3, q=1; FP64 AIRG setup + FGMRES(30) solve to rtol 1e-8")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, samples = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            samples += 1
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": samples}
+
+
+def run_oracle_sample(mesh: int, rtol: float):
+    """One oracle step (setup + solve) on a mesh x mesh instance of the workload; returns (dofs, seconds)."""
+    from oracle import oracle as O
+    from paper_2408_08262_gb300 import problems as P
+    p = P.blocked_sigma_2d(mesh)
+    t0 = time.perf_counter()
+    H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params())
+    x, info = H.solve(p.b, rtol=rtol)
+    dt = time.perf_counter() - t0
+    return p.n, dt, info
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    mesh = args.cpu_sample_mesh
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        run_oracle_sample(max(32, mesh // 4), args.rtol)
+    tot_dofs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        n, dt, info = run_oracle_sample(mesh, args.rtol)
+        tot_dofs += n
+        tot_t += dt
+    value = tot_dofs / tot_t
+    sample = (f"oracle setup+solve of the same generator at {mesh}x{mesh} ({6 * mesh * mesh:,} DOFs) per step, "
+              f"single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.mesh), "sample_mesh": mesh},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2408_08262_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2408_08262_gb300 import airg
+    from paper_2408_08262_gb300 import problems as P
+
+    p = P.blocked_sigma_2d(args.mesh)
+    rp_h = torch.from_numpy(p.rowptr).pin_memory()
+    ci_h = torch.from_numpy(p.col).pin_memory()
+    v_h = torch.from_numpy(p.val).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    rp, ci, v, b = (t.to(dev) for t in (rp_h, ci_h, v_h, b_h))
+    stream = torch.cuda.current_stream(dev)
+    params = airg.Params()
+    classes = airg.PROFILE_CLASSES
+
+    def step(profile=False):
+        H = airg.Hierarchy(rp, ci, v, params)
+        if profile:
+            H.profile()
+        x, info = H.solve(b, rtol=args.rtol)
+        kt = H.kernel_times() if profile else None
+        lv = H.level_info(-1)
+        H.close()
+        return info, kt, lv
+
+    # warm-up; the first warm-up step times every kernel class to find the dominant one
+    info0, kt0, lv0 = step(profile=True)
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    dominant = max(classes, key=lambda c: kt0[c]["ms"])
+
+    # timed region: K steps on the device, dominant kernel class timed with CUDA events
+    clk = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk.start()
+    launches0 = airg.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dom = {"launches": 0, "ms": 0.0, "bytes": 0.0}
+    solve_ms, setup_ms, iters = [], [], []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        H = airg.Hierarchy(rp, ci, v, params)
+        t1 = time.perf_counter()
+        H.profile([dominant])
+        x, info = H.solve(b, rtol=args.rtol)
+        t2 = time.perf_counter()
+        kt = H.kernel_times()[dominant]
+        H.close()
+        for k in dom:
+            dom[k] += kt[k]
+        setup_ms.append(1e3 * (t1 - t0))
+        solve_ms.append(1e3 * (t2 - t1))
+        iters.append(info["iters"])
+        if info["status"] != 0:
+            raise RuntimeError(f"solve did not converge: {info}")
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = airg.launch_count() - launches0
+    clocks = clk.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = p.n * args.steps * world / (t_ms / 1e3)
+
+    # end to end through the public API with host buffers: matrix and rhs copied in from pinned
+    # host memory, solution copied back, inside the timed region
+    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 8 + b_h.numel() * 8
+    d2h = x_h.numel() * 8
+    torch.cuda.synchronize(dev)
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        rp2, ci2, v2 = (t.to(dev, non_blocking=True) for t in (rp_h, ci_h, v_h))
+        H = airg.Hierarchy(rp2, ci2, v2, params)
+        H.solve_host(b_h, x_h, rtol=args.rtol)
+        H.close()
+    torch.cuda.synchronize(dev)
+    e_s = time.perf_counter() - e0
+    if dist:
+        tt = torch.tensor([e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_s = float(tt.item())
+    e2e = p.n * args.steps * world / e_s
+
+    peak, peak_kind = peaks()
+    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
+    per_launch_bytes = dom["bytes"] / max(1, dom["launches"])
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": per_launch_bytes,
+                "launches": dom["launches"], "avg_launch_us": 1e3 * dom["ms"] / max(1, dom["launches"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        n_s, dt_s, _ = run_oracle_sample(args.cpu_sample_mesh, args.rtol)
+        cpu = {"value": n_s / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle setup+solve of the same generator at {args.cpu_sample_mesh}x"
+                         f"{args.cpu_sample_mesh} ({n_s:,} DOFs), single thread, {dt_s:.1f} s"}
+
+    if rank == 0:
+        med = lambda a: sorted(a)[len(a) // 2]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name(args.mesh), "n": p.n, "nnz": p.nnz,
+                           "levels": lv0["levels"], "grid_complexity": round(lv0["grid"], 3),
+                           "operator_complexity": round(lv0["operator"], 3), "iters": med(iters),
+                           "setup_ms": round(med(setup_ms), 2), "solve_ms": round(med(solve_ms), 2),
+                           "solve_only_dofs_per_s": p.n / (med(solve_ms) / 1e3),
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

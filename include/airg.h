@@ -1,0 +1,188 @@
+/*
+ * airg.h -- C ABI of libairg.so: AIRG reduction multigrid (approximate ideal restriction with
+ * GMRES polynomials) as a preconditioner for GMRES, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Dargaville, Smedley-Stevenson, Smith & Pain, "Coarsening and parallelism with reduction
+ * multigrids for hyperbolic Boltzmann transport", arXiv 2408.08262:
+ *   - Section "CF splitting": strength of connection (eq. soc), PMISR (Algorithm 1) and the
+ *     diagonal-dominance cleanup DDC (Algorithm 2);
+ *   - Section "AIRG": per-level setup steps 1-11, the GMRES polynomial (eq. gmres_poly) with
+ *     first-order fixed sparsity (eq. fixed_sparsity), approximate ideal restriction
+ *     Z = -A_cf Ainv_ff (eq. prolong), one-point prolongation, A_c = R A P;
+ *   - Section "Results": V-cycle with up F-point smoothing only; Section "Timing results for
+ *     parallel optimisations": GMRES-polynomial coarse-grid solver.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are square CSR with int32 row pointers and column indices, columns sorted and
+ *     unique within each row, every diagonal entry stored and nonzero, FP64 values.
+ *   - Pointers named "device" must be CUDA device (or managed) memory on the current device;
+ *     pointers named "host" are ordinary host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All GPU work of a call is issued
+ *     on that stream; calls that must report sizes or convergence synchronise it.
+ *   - The caller owns every pointer it passes; the library never keeps a caller pointer after a
+ *     call returns (airg_setup copies the matrix).  A hierarchy owns all of its device memory.
+ *   - Return value: AIRG_OK (0), a negative AIRG_ERR_* code, or AIRG_NOT_CONVERGED (1).  The
+ *     library never aborts, traps or exits.  airg_status_string() names every code.
+ *   - Not thread-safe per hierarchy: one hierarchy must not be used by two calls at once.
+ */
+#ifndef AIRG_H
+#define AIRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* airg_stream_t; /* same object as cudaStream_t */
+
+enum {
+  AIRG_OK = 0,
+  AIRG_NOT_CONVERGED = 1,   /* solve hit max_it; x and info are still filled */
+  AIRG_ERR_ARG = -1,        /* null pointer, negative size, bad option value */
+  AIRG_ERR_CSR = -2,        /* row pointers not monotone, column out of range/unsorted/duplicate */
+  AIRG_ERR_ZERO_DIAG = -3,  /* a diagonal entry is missing or zero */
+  AIRG_ERR_NAN = -4,        /* NaN/Inf met in a norm during the solve */
+  AIRG_ERR_OOM = -5,        /* device allocation failed */
+  AIRG_ERR_CUDA = -6,       /* any other CUDA runtime error */
+  AIRG_ERR_UNSUPPORTED = -7 /* a product row exceeded the library's working-set limit */
+};
+
+enum { AIRG_FP64 = 0, AIRG_FP32 = 1, AIRG_BF16_VALUES = 2 };
+enum { AIRG_OUTER_FGMRES = 0, AIRG_OUTER_RICHARDSON = 1 };
+
+/* Square CSR matrix in device memory. */
+typedef struct {
+  int32_t n;              /* rows = columns */
+  int32_t nnz;            /* rowptr[n] */
+  const int32_t* rowptr;  /* device, n+1 */
+  const int32_t* col;     /* device, nnz, sorted unique per row */
+  const double* val;      /* device, nnz */
+} airg_csr;
+
+/* Setup parameters.  Defaults (airg_params_default) follow the paper's parallel settings
+ * (Section "Parallel results"): strength 0.5, n_loops^max = 3, DDC fraction 10 %, drop 0.01 on Z
+ * and 0.001 on the coarse matrices; two up F-smooths (Section "Results"); the coarse solve uses
+ * three iterations of a 12th-order fixed-sparsity polynomial (Section "Timing results"). */
+typedef struct {
+  double strong_threshold;  /* alpha in eq. soc, in [0, 1] */
+  double ddc_fraction;      /* fraction of F-points DDC converts, in [0, 1] */
+  int pmisr_max_loops;      /* n_loops^max of Algorithm 1; <= 0 means no cap */
+  int poly_order;           /* degree d of the GMRES polynomial on A_ff (m = d+1 coefficients) */
+  int coarse_poly_order;    /* degree of the coarsest-level polynomial */
+  int coarse_iters;         /* iterations of the coarsest-level polynomial solve (>= 1) */
+  int coarse_size;          /* a level with n <= coarse_size is the coarsest */
+  int max_levels;           /* hierarchy depth cap (>= 1) */
+  double drop_R;            /* relative row-wise inf-norm drop on Z */
+  double drop_Ac;           /* relative row-wise inf-norm drop on A_c (diagonal always kept) */
+  int n_smooth_up;          /* up F-point smooths per level */
+  int precision;            /* AIRG_FP64 (others reserved) */
+  int keep_setup;           /* 1: keep natural-numbering setup operators for airg_export_level */
+  uint64_t seed;            /* seeds PMISR weights and the Box-Muller right-hand sides */
+} airg_params;
+
+typedef struct airg_hierarchy airg_hierarchy; /* opaque, library-owned */
+
+typedef struct {
+  int outer;    /* AIRG_OUTER_FGMRES (right-preconditioned, CGS2) or AIRG_OUTER_RICHARDSON */
+  int restart;  /* FGMRES restart length, 1..32 */
+  int max_it;   /* maximum preconditioner applications */
+  double rtol;  /* stop when ||b - A x||_2 <= rtol ||b||_2 */
+  int x0_zero;  /* 1: ignore x on entry and start from zero */
+} airg_solve_opts;
+
+typedef struct {
+  int iters;      /* preconditioner applications (V-cycles) */
+  double relres;  /* true relative residual ||b - A x|| / ||b|| at exit */
+  int status;     /* same code as the return value */
+  int levels;     /* hierarchy levels */
+} airg_solve_info;
+
+/* Fills *p with the defaults above (seed 240808262). */
+void airg_params_default(airg_params* p);
+
+/* Builds the AIRG hierarchy of A (setup steps 1-11 of Section "AIRG" on every level, the
+ * coarsest-level polynomial, and the permuted solve-phase operators).  A's arrays are read on
+ * `stream` and copied; *out receives a new hierarchy, freed with airg_free.  Synchronises the
+ * stream several times per level (sizes of products).  Errors: AIRG_ERR_ARG, AIRG_ERR_CSR,
+ * AIRG_ERR_ZERO_DIAG, AIRG_ERR_OOM, AIRG_ERR_CUDA, AIRG_ERR_UNSUPPORTED; *out is NULL then. */
+int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out);
+
+/* Solves A x = b with the hierarchy as preconditioner.  b, x: device, n FP64.  x holds the initial
+ * guess on entry (unless opts->x0_zero) and the solution on exit.  Synchronises the stream once per
+ * iteration.  Returns AIRG_OK, AIRG_NOT_CONVERGED, or an error (x undefined on error). */
+int airg_solve(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* opts,
+               airg_solve_info* info, airg_stream_t stream);
+
+/* Same as airg_solve with b and x in HOST memory: copies b (and x) to the device, solves, copies
+ * x back; the copies run on `stream`. */
+int airg_solve_host(airg_hierarchy* H, const double* b_host, double* x_host, const airg_solve_opts* opts,
+                    airg_solve_info* info, airg_stream_t stream);
+
+/* One V-cycle from a zero guess, x = M b (b, x: device, n).  For tests and diagnostics. */
+int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t stream);
+
+/* The two-pass CF splitting alone (eq. soc, Algorithm 1, Algorithm 2) of one matrix, as done on
+ * level `level` of a setup (the level index salts the PMISR weight stream).  cf_out: device, n
+ * int8; 1 = F-point, 2 = C-point.  Synchronises the stream. */
+int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out, airg_stream_t stream);
+
+/* Frees a hierarchy and everything it owns (NULL is allowed).  Synchronises the stream the
+ * hierarchy was built on. */
+void airg_free(airg_hierarchy* H);
+
+/* Number of levels (>= 1), or a negative error. */
+int airg_num_levels(const airg_hierarchy* H);
+
+/* Per-level sizes into info[0..15] (host): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
+ * nnz(Z), coarsest flag, nnz(A_cf), fitted polynomial coefficients, nnz(AF solve operator),
+ * reserved (0) x4.  Level -1 gives totals: levels, grid complexity x1e6, operator complexity x1e6,
+ * storage complexity x1e6 (eq. mat_store), setup ms x1e3. */
+int airg_level_info(const airg_hierarchy* H, int level, int64_t* info);
+
+/* Copies a level operator to HOST arrays (sizes from airg_level_info).
+ * Natural numbering of the level (needs params.keep_setup = 1, else AIRG_ERR_ARG):
+ *   which 0 A, 1 A_ff, 2 A_fc, 3 A_cf, 5 Ainv, 6 Z (rows: C-points in ascending order, columns:
+ *   F-points in ascending order).
+ * Solve-phase layout (always available): 7 [A_ff A_fc] rows of the F-points with columns in the
+ *   level's F-then-C numbering (nnz = info[11]), 8 Z with rows in the next level's F-then-C
+ *   numbering, 9 the top-level matrix permuted to level 0's F-then-C numbering (n0 x n0, nnz of
+ *   the input), 10 Ainv as used by the solve, 11 coarsest-level matrix.
+ * Any of rowptr/col/val may be NULL. */
+int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowptr, int32_t* col, double* val);
+
+/* Copies level vectors to HOST arrays: cf (n int8, 1 F / 2 C; NULL on the coarsest level),
+ * w (n_f int32: C index of each F-point's one-point interpolation source, -1 for none), alpha
+ * (fitted polynomial coefficients, poly_order+1 or coarse_poly_order+1 doubles).  Needs
+ * keep_setup for cf and w. */
+int airg_export_vectors(const airg_hierarchy* H, int level, int8_t* cf, int32_t* w, double* alpha);
+
+/* Copies the solve-phase numbering of a level to HOST arrays: pos (n entries; natural index of
+ * the level -> nested position: F-points first in ascending order, then the C-points in the next
+ * level's nested numbering; identity on the coarsest level) and
+ * w_solve (n_f entries; one-point source of each F-point in the next level's solve numbering,
+ * -1 for none).  Either may be NULL. */
+int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t* w_solve);
+
+/* Kernel timing for roofline reports.  `enable` is a bit mask of kernel classes (bit c = class c;
+ * 0 disables, -1 times every class).  Every launch of a selected class is bracketed by CUDA events
+ * on its stream; airg_kernel_times() returns, per kernel
+ * class (0: smoother residual A_F*, 1: smoother update Ainv, 2: restriction Z, 3: top-level
+ * operator, 4: coarsest level, 5: prolongation gather, 6: Gram-Schmidt passes), the launch count,
+ * the summed milliseconds and the summed algorithmic bytes (CSR arrays + vectors read/written
+ * once).  Every call of airg_profile_enable resets the sums. */
+int airg_profile_enable(airg_hierarchy* H, int enable);
+int airg_kernel_times(airg_hierarchy* H, int64_t* launches, double* ms, double* bytes, int nclasses);
+
+/* Total number of CUDA kernel launches this library has issued in the process (all hierarchies,
+ * all calls).  Used to count the GPU work of a timed region. */
+int64_t airg_launch_count(void);
+
+/* Human-readable name of a status code. */
+const char* airg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIRG_H */

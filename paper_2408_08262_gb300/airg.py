@@ -1,0 +1,275 @@
+"""Thin Python binding of libairg.so (the C ABI in include/airg.h).
+
+Argument marshalling only: every step of setup and solve runs in the library's CUDA kernels.
+PyTorch provides device memory and the current stream.  There is no CPU fallback: if the
+compiled library is missing, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libairg.so")
+_lib = None
+
+AIRG_OK, AIRG_NOT_CONVERGED = 0, 1
+STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR", -3: "zero diagonal",
+          -4: "NaN", -5: "out of memory", -6: "CUDA error", -7: "unsupported"}
+PROFILE_CLASSES = ["smooth_resid", "smooth_update", "restrict", "top_op", "coarsest", "prolong", "gram_schmidt"]
+
+
+class AirgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("strong_threshold", C.c_double), ("ddc_fraction", C.c_double), ("pmisr_max_loops", C.c_int),
+                ("poly_order", C.c_int), ("coarse_poly_order", C.c_int), ("coarse_iters", C.c_int),
+                ("coarse_size", C.c_int), ("max_levels", C.c_int), ("drop_R", C.c_double), ("drop_Ac", C.c_double),
+                ("n_smooth_up", C.c_int), ("precision", C.c_int), ("keep_setup", C.c_int), ("seed", C.c_uint64)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("outer", C.c_int), ("restart", C.c_int), ("max_it", C.c_int), ("rtol", C.c_double),
+                ("x0_zero", C.c_int)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("status", C.c_int), ("levels", C.c_int)]
+
+
+def lib():
+    """Loads libairg.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libairg.so not built ({LIB_PATH}); run paper_2408_08262_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.airg_setup.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts), C.POINTER(_Info), C.c_void_p]
+        L.airg_solve_host.argtypes = L.airg_solve.argtypes
+        L.airg_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.airg_cf_split.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
+        L.airg_free.argtypes = [C.c_void_p]
+        L.airg_free.restype = None
+        L.airg_num_levels.argtypes = [C.c_void_p]
+        L.airg_level_info.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.airg_export_csr.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.airg_export_vectors.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.airg_export_layout.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        L.airg_profile_enable.argtypes = [C.c_void_p, C.c_int]
+        L.airg_kernel_times.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.airg_status_string.restype = C.c_char_p
+        L.airg_launch_count.restype = C.c_int64
+        L.airg_params_default.argtypes = [C.POINTER(_Params)]
+        L.airg_params_default.restype = None
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["airg_params_default", "airg_setup", "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
+            "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
+            "airg_profile_enable", "airg_kernel_times", "airg_launch_count", "airg_status_string"]
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libairg.so so far in this process."""
+    return int(lib().airg_launch_count())
+
+
+@dataclass
+class Params:
+    strong_threshold: float = 0.5
+    ddc_fraction: float = 0.1
+    pmisr_max_loops: int = 3
+    poly_order: int = 2
+    coarse_poly_order: int = 12
+    coarse_iters: int = 3
+    coarse_size: int = 64
+    max_levels: int = 64
+    drop_R: float = 0.01
+    drop_Ac: float = 0.001
+    n_smooth_up: int = 2
+    precision: int = 0
+    keep_setup: int = 0
+    seed: int = 240808262
+
+    def c(self) -> _Params:
+        return _Params(**{k: getattr(self, k) for k, _ in _Params._fields_})
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, what: str, allow_not_converged: bool = False):
+    if code == AIRG_OK or (allow_not_converged and code == AIRG_NOT_CONVERGED):
+        return
+    raise AirgError(code, what)
+
+
+def _csr(rowptr, col, val) -> _Csr:
+    import torch
+    for t, dt in ((rowptr, torch.int32), (col, torch.int32), (val, torch.float64)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("CSR arrays must be contiguous CUDA tensors (int32, int32, float64)")
+    return _Csr(rowptr.numel() - 1, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+
+class Hierarchy:
+    """An AIRG hierarchy built on the GPU (airg_setup)."""
+
+    def __init__(self, rowptr, col, val, params: Params | None = None, stream=None):
+        self.params = params or Params()
+        self._keep = (rowptr, col, val)
+        A = _csr(rowptr, col, val)
+        self.n = A.n
+        h = C.c_void_p()
+        _check(lib().airg_setup(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)), "airg_setup")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().airg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_levels(self) -> int:
+        return lib().airg_num_levels(self._h)
+
+    def level_info(self, level: int) -> dict:
+        info = np.zeros(16, dtype=np.int64)
+        _check(lib().airg_level_info(self._h, level, info.ctypes.data), "airg_level_info")
+        if level == -1:
+            return dict(levels=int(info[0]), grid=info[1] / 1e6, operator=info[2] / 1e6, storage=info[3] / 1e6,
+                        setup_ms=info[4] / 1e3)
+        keys = ["n", "nnz", "nf", "nc", "nnz_aff", "nnz_afc", "nnz_ainv", "nnz_z", "coarsest", "nnz_acf",
+                "alpha_fitted", "nnz_af"]
+        return {k: int(v) for k, v in zip(keys, info)}
+
+    def solve(self, b, x=None, outer: str = "fgmres", restart: int = 30, max_it: int = 200, rtol: float = 1e-10,
+              stream=None):
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+            x0_zero = 1
+        else:
+            x0_zero = 0
+        opts = _Opts({"fgmres": 0, "richardson": 1}[outer], restart, max_it, rtol, x0_zero)
+        info = _Info()
+        rc = lib().airg_solve(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), C.byref(opts),
+                              C.byref(info), _stream(stream))
+        _check(rc, "airg_solve", allow_not_converged=True)
+        return x, dict(iters=info.iters, relres=info.relres, status=info.status, levels=info.levels)
+
+    def solve_host(self, b_host, x_host, outer="fgmres", restart=30, max_it=200, rtol=1e-10, x0_zero=True,
+                   stream=None):
+        """b_host, x_host: CPU tensors (ideally pinned), float64; copies run inside the call."""
+        opts = _Opts({"fgmres": 0, "richardson": 1}[outer], restart, max_it, rtol, int(x0_zero))
+        info = _Info()
+        rc = lib().airg_solve_host(self._h, C.c_void_p(b_host.data_ptr()), C.c_void_p(x_host.data_ptr()),
+                                   C.byref(opts), C.byref(info), _stream(stream))
+        _check(rc, "airg_solve_host", allow_not_converged=True)
+        return x_host, dict(iters=info.iters, relres=info.relres, status=info.status, levels=info.levels)
+
+    def vcycle(self, b, stream=None):
+        import torch
+        x = torch.empty_like(b)
+        _check(lib().airg_vcycle(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), _stream(stream)),
+               "airg_vcycle")
+        return x
+
+    def export(self, level: int, which: str):
+        """which: A, Aff, Afc, Acf, Ainv, Z (natural numbering, needs keep_setup) or the solve layout
+        AF_solve, Z_solve, A0_solve, Ainv_solve, A_coarsest."""
+        code = {"A": 0, "Aff": 1, "Afc": 2, "Acf": 3, "Ainv": 5, "Z": 6, "AF_solve": 7, "Z_solve": 8,
+                "A0_solve": 9, "Ainv_solve": 10, "A_coarsest": 11}[which]
+        inf = self.level_info(level)
+        top = self.level_info(0)
+        rows = {"A": inf["n"], "Aff": inf["nf"], "Afc": inf["nf"], "Acf": inf["nc"], "Z": inf["nc"],
+                "Ainv": inf["n"] if inf["coarsest"] else inf["nf"], "AF_solve": inf["nf"], "Z_solve": inf["nc"],
+                "A0_solve": top["n"], "Ainv_solve": inf["n"] if inf["coarsest"] else inf["nf"],
+                "A_coarsest": inf["n"]}[which]
+        nnz = {"A": inf["nnz"], "Aff": inf["nnz_aff"], "Afc": inf["nnz_afc"], "Acf": inf["nnz_acf"],
+               "Z": inf["nnz_z"], "Ainv": inf["nnz_ainv"], "AF_solve": inf["nnz_af"], "Z_solve": inf["nnz_z"],
+               "A0_solve": top["nnz"], "Ainv_solve": inf["nnz_ainv"], "A_coarsest": inf["nnz"]}[which]
+        rp = np.zeros(rows + 1, dtype=np.int32)
+        ci = np.zeros(nnz, dtype=np.int32)
+        v = np.zeros(nnz, dtype=np.float64)
+        _check(lib().airg_export_csr(self._h, level, code, rp.ctypes.data, ci.ctypes.data, v.ctypes.data),
+               "airg_export_csr")
+        return rp, ci, v
+
+    def vectors(self, level: int) -> dict:
+        inf = self.level_info(level)
+        m = (self.params.coarse_poly_order if inf["coarsest"] else self.params.poly_order) + 1
+        cf = np.zeros(0 if inf["coarsest"] else inf["n"], dtype=np.int8)
+        w = np.zeros(inf["nf"], dtype=np.int32)
+        alpha = np.zeros(m, dtype=np.float64)
+        keep = bool(self.params.keep_setup)
+        _check(lib().airg_export_vectors(self._h, level, cf.ctypes.data if keep else None,
+                                         w.ctypes.data if keep else None, alpha.ctypes.data), "airg_export_vectors")
+        return dict(cf=cf, w=w, alpha=alpha)
+
+    def layout(self, level: int) -> dict:
+        inf = self.level_info(level)
+        pos = np.zeros(inf["n"], dtype=np.int32)
+        ws = np.zeros(inf["nf"], dtype=np.int32)
+        _check(lib().airg_export_layout(self._h, level, pos.ctypes.data, ws.ctypes.data), "airg_export_layout")
+        return dict(pos=pos, w_solve=ws)
+
+    def profile(self, classes=None):
+        """Times kernel classes with CUDA events: None = all, [] = off, or a list of class names."""
+        if classes is None:
+            mask = -1
+        else:
+            mask = 0
+            for c in classes:
+                mask |= 1 << PROFILE_CLASSES.index(c)
+        _check(lib().airg_profile_enable(self._h, mask), "airg_profile_enable")
+
+    def kernel_times(self) -> dict:
+        n = len(PROFILE_CLASSES)
+        la = np.zeros(n, dtype=np.int64)
+        ms = np.zeros(n)
+        by = np.zeros(n)
+        _check(lib().airg_kernel_times(self._h, la.ctypes.data, ms.ctypes.data, by.ctypes.data, n), "airg_kernel_times")
+        return {c: dict(launches=int(la[i]), ms=float(ms[i]), bytes=float(by[i])) for i, c in enumerate(PROFILE_CLASSES)}
+
+
+def cf_split(rowptr, col, val, params: Params | None = None, level: int = 0, stream=None):
+    """Two-pass CF splitting on the GPU; returns a CUDA int8 tensor (1 = F, 2 = C)."""
+    import torch
+    A = _csr(rowptr, col, val)
+    cf = torch.empty(A.n, dtype=torch.int8, device=rowptr.device)
+    p = params or Params()
+    _check(lib().airg_cf_split(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf.data_ptr()), _stream(stream)),
+           "airg_cf_split")
+    return cf
+
+
+def setup(rowptr, col, val, params: Params | None = None, stream=None) -> Hierarchy:
+    return Hierarchy(rowptr, col, val, params, stream)
+
+
+def solve(H: Hierarchy, b, **kw):
+    return H.solve(b, **kw)

@@ -1,0 +1,480 @@
+// C ABI of libairg.so (declared in include/airg.h): hierarchy construction, solves, CF-splitting
+// and export hooks, kernel timing.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "airg_hier.cuh"
+
+using namespace airg;
+
+namespace airg {
+std::atomic<long long> g_launches{0};
+}
+
+namespace {
+
+SetupParams to_setup(const airg_params& p) {
+  SetupParams q;
+  q.strong_threshold = p.strong_threshold;
+  q.ddc_fraction = p.ddc_fraction;
+  q.drop_R = p.drop_R;
+  q.drop_Ac = p.drop_Ac;
+  q.pmisr_max_loops = p.pmisr_max_loops;
+  q.poly_order = p.poly_order;
+  q.coarse_poly_order = p.coarse_poly_order;
+  q.coarse_iters = p.coarse_iters;
+  q.coarse_size = p.coarse_size;
+  q.max_levels = p.max_levels;
+  q.n_smooth_up = p.n_smooth_up;
+  q.seed = p.seed;
+  return q;
+}
+
+int check_params(const airg_params* p) {
+  if (!p) return AIRG_ERR_ARG;
+  if (!(p->strong_threshold >= 0.0 && p->strong_threshold <= 1.0)) return AIRG_ERR_ARG;
+  if (!(p->ddc_fraction >= 0.0 && p->ddc_fraction <= 1.0)) return AIRG_ERR_ARG;
+  if (p->poly_order < 0 || p->poly_order > 14 || p->coarse_poly_order < 0 || p->coarse_poly_order > 14) return AIRG_ERR_ARG;
+  if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0 || p->coarse_size < 0) return AIRG_ERR_ARG;
+  if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
+  if (p->precision != AIRG_FP64) return AIRG_ERR_ARG;
+  return AIRG_OK;
+}
+
+// columns referenced at least once: the x traffic of an SpMV counted once per distinct column
+__global__ void k_touch(int nnz, const int* __restrict__ ci, unsigned char* __restrict__ flag) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+    flag[ci[k]] = 1;
+}
+__global__ void k_count_flags(int n, const unsigned char* __restrict__ flag, int* cnt) {
+  int c = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c += flag[i];
+  if (c) atomicAdd(cnt, c);
+}
+
+// Algorithmic bytes of one SpMV with the given epilogue: CSR arrays once, each referenced x entry
+// once, y written once, b (RESID/ADDB) or y (ADD) read once.
+int spmv_bytes(const DCsr& A, bool reads_extra, Arena& tmp, cudaStream_t s, double* out) {
+  unsigned char* flag;
+  int* cnt;
+  AIRG_TRY(tmp.alloc(&flag, std::max(A.ncols, 1)));
+  AIRG_TRY(tmp.alloc(&cnt, 1));
+  CU_TRY(cudaMemsetAsync(flag, 0, std::max(A.ncols, 1), s));
+  CU_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+  if (A.nnz > 0) airg::note_launch(), k_touch<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.nnz, A.ci, flag);
+  if (A.ncols > 0) airg::note_launch(), k_count_flags<<<grid_for(A.ncols, 256), 256, 0, s>>>(A.ncols, flag, cnt);
+  CU_TRY(cudaGetLastError());
+  int h = 0;
+  CU_TRY(cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  *out = 12.0 * A.nnz + 4.0 * (A.nrows + 1) + 8.0 * h + 8.0 * A.nrows * (reads_extra ? 2 : 1);
+  return AIRG_OK;
+}
+
+int copy_csr(const DCsr& A, DCsr& B, Arena& a, cudaStream_t s) {
+  AIRG_TRY(a.csr(B, A.nrows, A.ncols, A.nnz));
+  CU_TRY(cudaMemcpyAsync(B.rp, A.rp, sizeof(int) * ((size_t)A.nrows + 1), cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(B.ci, A.ci, sizeof(int) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(B.v, A.v, sizeof(double) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, s));
+  return AIRG_OK;
+}
+
+double avg_len(const DCsr& A) { return A.nrows > 0 ? (double)A.nnz / A.nrows : 1.0; }
+
+int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
+  cudaStream_t s = H->s;
+  const SetupParams sp = to_setup(H->p);
+  Arena tmp;
+  tmp.s = s;
+  struct Rel {
+    Arena& a;
+    ~Rel() { a.release(); }
+  } rel{tmp};
+  DCsr A0;
+  AIRG_TRY(H->setup_mem.csr(A0, Ain->n, Ain->n, Ain->nnz));
+  CU_TRY(cudaMemcpyAsync(A0.rp, Ain->rowptr, sizeof(int) * ((size_t)Ain->n + 1), cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(A0.ci, Ain->col, sizeof(int) * (size_t)Ain->nnz, cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(A0.v, Ain->val, sizeof(double) * (size_t)Ain->nnz, cudaMemcpyDeviceToDevice, s));
+  AIRG_TRY(validate_csr(A0, tmp, s));
+  H->n0 = Ain->n;
+  H->top_nnz = Ain->nnz;
+  DCsr A = A0;
+  for (int l = 0;; ++l) {
+    LevelBuild L;
+    DCsr Ac;
+    Arena lt;
+    lt.s = s;
+    int rc = build_level(A, sp, l, l == sp.max_levels - 1, L, Ac, H->setup_mem, lt, s);
+    lt.release();
+    if (rc != AIRG_OK) return rc;
+    H->lb.push_back(L);
+    if (L.coarsest) break;
+    A = Ac;
+  }
+  // solve-phase operators
+  const int nl = (int)H->lb.size();
+  H->lv.resize(nl);
+  // nested numberings, from the coarsest level upwards
+  for (int l = nl - 2; l >= 0; --l) {
+    const int* lay_next = (l + 1 < nl - 1) ? H->lv[l + 1].lay : nullptr;
+    AIRG_TRY(H->solve_mem.alloc(&H->lv[l].lay, std::max(H->lb[l].n, 1)));
+    AIRG_TRY(compose_layout(H->lb[l], lay_next, H->lv[l].lay, s));
+  }
+  long long off = 0;
+  for (int l = 0; l < nl; ++l) {
+    LevelBuild& L = H->lb[l];
+    SolveLevel& S = H->lv[l];
+    S.n = L.n;
+    S.off = off;
+    S.coarsest = L.coarsest;
+    if (L.coarsest) {
+      AIRG_TRY(copy_csr(L.A, S.A, H->solve_mem, s));
+      AIRG_TRY(copy_csr(L.Ainv, S.Ainv, H->solve_mem, s));
+      S.lanes_A = pick_lanes(avg_len(S.A));
+      S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
+      AIRG_TRY(spmv_bytes(S.A, true, tmp, s, &S.bytes_A));
+      AIRG_TRY(spmv_bytes(S.Ainv, true, tmp, s, &S.bytes_Ainv));
+      break;
+    }
+    S.nf = L.nf;
+    S.nc = L.nc;
+    const int* lay_next = (l + 1 < nl - 1) ? H->lv[l + 1].lay : nullptr;
+    AIRG_TRY(build_solve_ops(L, lay_next, S.AF, S.Z, &S.w, H->solve_mem, tmp, s));
+    AIRG_TRY(copy_csr(L.Ainv, S.Ainv, H->solve_mem, s));
+    S.lanes_AF = pick_lanes(avg_len(S.AF));
+    S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
+    S.lanes_Z = pick_lanes(avg_len(S.Z));
+    AIRG_TRY(spmv_bytes(S.AF, true, tmp, s, &S.bytes_AF));
+    AIRG_TRY(spmv_bytes(S.Ainv, true, tmp, s, &S.bytes_Ainv));
+    AIRG_TRY(spmv_bytes(S.Z, true, tmp, s, &S.bytes_Z));
+    off += L.nf;
+  }
+  // top-level operator in the nested solve numbering of level 0
+  if (!H->lb[0].coarsest) {
+    H->pos0 = H->lv[0].lay;
+    AIRG_TRY(permute_matrix(A0, H->pos0, H->A0s, H->solve_mem, tmp, s));
+  } else {
+    AIRG_TRY(copy_csr(A0, H->A0s, H->solve_mem, s));
+    H->pos0 = nullptr;
+  }
+  H->lanes_A0 = pick_lanes(avg_len(H->A0s));
+  AIRG_TRY(spmv_bytes(H->A0s, false, tmp, s, &H->bytes_A0));
+  // complexities (Section "Strong tolerances"; storage complexity eq. mat_store)
+  double gs = 0, os = 0, st = 0;
+  for (int l = 0; l < nl; ++l) {
+    const LevelBuild& L = H->lb[l];
+    gs += L.n;
+    os += L.A.nnz;
+    if (L.coarsest) st += L.Ainv.nnz + (H->p.coarse_iters > 1 ? L.A.nnz : 0);
+    else st += (double)L.Ainv.nnz + L.Aff.nnz + L.Afc.nnz + (L.Z.nnz + (double)L.nc) + ((double)L.nc + L.nf);
+  }
+  // the prolongator count above is an upper bound (F rows without a C neighbour have no entry)
+  H->grid_cx = H->n0 > 0 ? gs / H->n0 : 0;
+  H->op_cx = H->top_nnz > 0 ? os / H->top_nnz : 0;
+  H->storage_cx = H->top_nnz > 0 ? st / H->top_nnz : 0;
+  CU_TRY(cudaStreamSynchronize(s));
+  H->alphas.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    H->alphas[l].assign(H->lb[l].m, 0.0);
+    if (H->lb[l].m) CU_TRY(cudaMemcpy(H->alphas[l].data(), H->lb[l].alpha, sizeof(double) * H->lb[l].m, cudaMemcpyDeviceToHost));
+  }
+  if (!H->p.keep_setup) {
+    H->setup_mem.release();
+    for (auto& L : H->lb) {
+      // keep the sizes for airg_level_info; drop the pointers
+      L.A.rp = L.A.ci = nullptr; L.A.v = nullptr;
+      L.cf = nullptr; L.pos = L.Fnat = L.Cnat = nullptr; L.w = nullptr;
+      L.Aff.rp = L.Aff.ci = nullptr; L.Afc.rp = L.Afc.ci = nullptr; L.Acf.rp = L.Acf.ci = nullptr;
+      L.Z.rp = L.Z.ci = nullptr; L.Ainv.rp = L.Ainv.ci = nullptr;
+      L.Aff.v = L.Afc.v = L.Acf.v = L.Z.v = L.Ainv.v = nullptr;
+      L.alpha = nullptr;
+    }
+    H->kept = false;
+  } else {
+    H->kept = true;
+  }
+  return AIRG_OK;
+}
+
+void destroy(airg_hierarchy* H) {
+  if (!H) return;
+  cudaStreamSynchronize(H->s);
+  H->solve_mem.release();
+  H->setup_mem.release();
+  cudaStreamSynchronize(H->s);
+  for (auto e : H->prof.pool) cudaEventDestroy(e);
+  if (H->hsc) cudaFreeHost(H->hsc);
+  delete H;
+}
+
+int check_csr_arg(const airg_csr* A) {
+  if (!A || A->n < 0 || A->nnz < 0) return AIRG_ERR_ARG;
+  if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val)))) return AIRG_ERR_ARG;
+  return AIRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void airg_params_default(airg_params* p) {
+  if (!p) return;
+  p->strong_threshold = 0.5;
+  p->ddc_fraction = 0.1;
+  p->pmisr_max_loops = 3;
+  p->poly_order = 2;
+  p->coarse_poly_order = 12;
+  p->coarse_iters = 3;
+  p->coarse_size = 64;
+  p->max_levels = 64;
+  p->drop_R = 0.01;
+  p->drop_Ac = 0.001;
+  p->n_smooth_up = 2;
+  p->precision = AIRG_FP64;
+  p->keep_setup = 0;
+  p->seed = 240808262ULL;
+}
+
+int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
+  if (!out) return AIRG_ERR_ARG;
+  *out = nullptr;
+  AIRG_TRY(check_csr_arg(A));
+  AIRG_TRY(check_params(p));
+  if (A->n == 0) return AIRG_ERR_ARG;
+  airg_hierarchy* H = new (std::nothrow) airg_hierarchy;
+  if (!H) return AIRG_ERR_OOM;
+  H->p = *p;
+  H->s = (cudaStream_t)stream;
+  H->solve_mem.s = H->s;
+  H->setup_mem.s = H->s;
+  {
+    // keep freed stream-ordered allocations cached in the pool between setup phases
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ULL;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = setup_impl(H, A);
+  if (rc != AIRG_OK) {
+    cudaGetLastError();
+    destroy(H);
+    return rc;
+  }
+  H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = H;
+  return AIRG_OK;
+}
+
+int airg_solve(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* opts, airg_solve_info* info,
+               airg_stream_t stream) {
+  if (!H || !b || !x || !opts) return AIRG_ERR_ARG;
+  if (opts->restart < 1 || opts->restart > 32 || opts->max_it < 0 || !(opts->rtol >= 0.0)) return AIRG_ERR_ARG;
+  airg_solve_info local{};
+  airg_solve_info* inf = info ? info : &local;
+  H->s = (cudaStream_t)stream;
+  H->solve_mem.s = H->s;
+  inf->levels = (int)H->lv.size();
+  int rc;
+  if (opts->outer == AIRG_OUTER_RICHARDSON) rc = solve_richardson(H, b, x, opts, inf);
+  else if (opts->outer == AIRG_OUTER_FGMRES) rc = solve_fgmres(H, b, x, opts, inf);
+  else return AIRG_ERR_ARG;
+  inf->status = rc;
+  return rc;
+}
+
+int airg_solve_host(airg_hierarchy* H, const double* b_host, double* x_host, const airg_solve_opts* opts,
+                    airg_solve_info* info, airg_stream_t stream) {
+  if (!H || !b_host || !x_host || !opts) return AIRG_ERR_ARG;
+  H->s = (cudaStream_t)stream;
+  H->solve_mem.s = H->s;
+  if (!H->hb) {
+    AIRG_TRY(H->solve_mem.alloc(&H->hb, std::max(H->n0, 1)));
+    AIRG_TRY(H->solve_mem.alloc(&H->hx, std::max(H->n0, 1)));
+  }
+  const size_t bytes = sizeof(double) * (size_t)H->n0;
+  CU_TRY(cudaMemcpyAsync(H->hb, b_host, bytes, cudaMemcpyHostToDevice, H->s));
+  if (!opts->x0_zero) CU_TRY(cudaMemcpyAsync(H->hx, x_host, bytes, cudaMemcpyHostToDevice, H->s));
+  int rc = airg_solve(H, H->hb, H->hx, opts, info, stream);
+  if (rc < 0) return rc;
+  CU_TRY(cudaMemcpyAsync(x_host, H->hx, bytes, cudaMemcpyDeviceToHost, H->s));
+  CU_TRY(cudaStreamSynchronize(H->s));
+  return rc;
+}
+
+int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t stream) {
+  if (!H || !b || !x) return AIRG_ERR_ARG;
+  H->s = (cudaStream_t)stream;
+  H->solve_mem.s = H->s;
+  AIRG_TRY(solve_alloc(H, 1));
+  if (H->pos0) dev_permute(b, H->pos0, H->bp, H->n0, false, H->s);
+  else CU_TRY(cudaMemcpyAsync(H->bp, b, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s));
+  AIRG_TRY(vcycle_solve_order(H, H->bp, H->xp));
+  if (H->pos0) dev_permute(H->xp, H->pos0, x, H->n0, true, H->s);
+  else CU_TRY(cudaMemcpyAsync(x, H->xp, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s));
+  CU_TRY(cudaGetLastError());
+  CU_TRY(cudaStreamSynchronize(H->s));
+  AIRG_TRY(prof_flush(H));
+  return AIRG_OK;
+}
+
+int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out, airg_stream_t stream) {
+  AIRG_TRY(check_csr_arg(A));
+  AIRG_TRY(check_params(p));
+  if (!cf_out || level < 0) return AIRG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena tmp;
+  tmp.s = s;
+  DCsr D;
+  D.nrows = D.ncols = A->n;
+  D.nnz = A->nnz;
+  D.rp = const_cast<int*>(A->rowptr);
+  D.ci = const_cast<int*>(A->col);
+  D.v = const_cast<double*>(A->val);
+  int rc = validate_csr(D, tmp, s);
+  int nf = 0;
+  if (rc == AIRG_OK) rc = cf_split(D, to_setup(*p), level, cf_out, nullptr, &nf, tmp, s);
+  if (rc == AIRG_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  tmp.release();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+void airg_free(airg_hierarchy* H) { destroy(H); }
+
+int airg_num_levels(const airg_hierarchy* H) { return H ? (int)H->lv.size() : AIRG_ERR_ARG; }
+
+int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
+  if (!H || !info) return AIRG_ERR_ARG;
+  for (int i = 0; i < 16; ++i) info[i] = 0;
+  if (level == -1) {
+    info[0] = (int64_t)H->lv.size();
+    info[1] = (int64_t)std::llround(H->grid_cx * 1e6);
+    info[2] = (int64_t)std::llround(H->op_cx * 1e6);
+    info[3] = (int64_t)std::llround(H->storage_cx * 1e6);
+    info[4] = (int64_t)std::llround(H->setup_ms * 1e3);
+    return AIRG_OK;
+  }
+  if (level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
+  const LevelBuild& L = H->lb[level];
+  const SolveLevel& S = H->lv[level];
+  info[0] = L.n;
+  info[1] = L.A.nnz;
+  info[2] = L.nf;
+  info[3] = L.nc;
+  info[4] = L.Aff.nnz;
+  info[5] = L.Afc.nnz;
+  info[6] = L.Ainv.nnz;
+  info[7] = L.Z.nnz;
+  info[8] = L.coarsest ? 1 : 0;
+  info[9] = L.Acf.nnz;
+  info[10] = L.fitted;
+  info[11] = S.AF.nnz;
+  return AIRG_OK;
+}
+
+int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowptr, int32_t* col, double* val) {
+  if (!H || level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
+  if (which < 7 && !H->kept) return AIRG_ERR_ARG;
+  const LevelBuild& L = H->lb[level];
+  const SolveLevel& S = H->lv[level];
+  const DCsr* M = nullptr;
+  switch (which) {
+    case 7: M = &S.AF; break;
+    case 8: M = &S.Z; break;
+    case 9: M = &H->A0s; break;
+    case 10: M = &S.Ainv; break;
+    case 11: M = &S.A; break;
+    case 0: M = &L.A; break;
+    case 1: M = &L.Aff; break;
+    case 2: M = &L.Afc; break;
+    case 3: M = &L.Acf; break;
+    case 5: M = &L.Ainv; break;
+    case 6: M = &L.Z; break;
+    default: return AIRG_ERR_ARG;
+  }
+  if (L.coarsest && which != 0 && which != 5 && which != 9 && which != 10 && which != 11) return AIRG_ERR_ARG;
+  if (!L.coarsest && which == 11) return AIRG_ERR_ARG;
+  cudaStream_t s = H->s;
+  if (rowptr) CU_TRY(cudaMemcpyAsync(rowptr, M->rp, sizeof(int) * ((size_t)M->nrows + 1), cudaMemcpyDeviceToHost, s));
+  if (col && M->nnz) CU_TRY(cudaMemcpyAsync(col, M->ci, sizeof(int) * (size_t)M->nnz, cudaMemcpyDeviceToHost, s));
+  if (val && M->nnz) CU_TRY(cudaMemcpyAsync(val, M->v, sizeof(double) * (size_t)M->nnz, cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  return AIRG_OK;
+}
+
+int airg_export_vectors(const airg_hierarchy* H, int level, int8_t* cf, int32_t* w, double* alpha) {
+  if (!H || level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
+  const LevelBuild& L = H->lb[level];
+  cudaStream_t s = H->s;
+  if ((cf || w) && !H->kept) return AIRG_ERR_ARG;
+  if (cf && !L.coarsest) CU_TRY(cudaMemcpyAsync(cf, L.cf, (size_t)L.n, cudaMemcpyDeviceToHost, s));
+  if (w && !L.coarsest && L.nf) CU_TRY(cudaMemcpyAsync(w, L.w, sizeof(int) * (size_t)L.nf, cudaMemcpyDeviceToHost, s));
+  if (alpha)
+    for (size_t k = 0; k < H->alphas[level].size(); ++k) alpha[k] = H->alphas[level][k];
+  CU_TRY(cudaStreamSynchronize(s));
+  return AIRG_OK;
+}
+
+int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t* w_solve) {
+  if (!H || level < 0 || level >= (int)H->lv.size()) return AIRG_ERR_ARG;
+  const SolveLevel& S = H->lv[level];
+  cudaStream_t s = H->s;
+  if (pos) {
+    if (!S.coarsest && S.lay) CU_TRY(cudaMemcpyAsync(pos, S.lay, sizeof(int) * (size_t)S.n, cudaMemcpyDeviceToHost, s));
+    else
+      for (int i = 0; i < S.n; ++i) pos[i] = i;
+  }
+  if (w_solve && !S.coarsest && S.nf)
+    CU_TRY(cudaMemcpyAsync(w_solve, S.w, sizeof(int) * (size_t)S.nf, cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  return AIRG_OK;
+}
+
+int airg_profile_enable(airg_hierarchy* H, int enable) {
+  if (!H) return AIRG_ERR_ARG;
+  H->prof.on = enable != 0;
+  H->prof.mask = (unsigned)enable;
+  for (int c = 0; c < PC_N; ++c) {
+    H->prof.launches[c] = 0;
+    H->prof.ms[c] = 0.0;
+    H->prof.bytes[c] = 0.0;
+  }
+  return AIRG_OK;
+}
+
+int airg_kernel_times(airg_hierarchy* H, int64_t* launches, double* ms, double* bytes, int nclasses) {
+  if (!H || nclasses < 0) return AIRG_ERR_ARG;
+  AIRG_TRY(prof_flush(H));
+  for (int c = 0; c < nclasses && c < PC_N; ++c) {
+    if (launches) launches[c] = H->prof.launches[c];
+    if (ms) ms[c] = H->prof.ms[c];
+    if (bytes) bytes[c] = H->prof.bytes[c];
+  }
+  return AIRG_OK;
+}
+
+int64_t airg_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char* airg_status_string(int status) {
+  switch (status) {
+    case AIRG_OK: return "ok";
+    case AIRG_NOT_CONVERGED: return "not converged (max_it reached)";
+    case AIRG_ERR_ARG: return "invalid argument";
+    case AIRG_ERR_CSR: return "invalid CSR (row pointers, column range, order or duplicates)";
+    case AIRG_ERR_ZERO_DIAG: return "missing or zero diagonal entry";
+    case AIRG_ERR_NAN: return "NaN or Inf in the solve";
+    case AIRG_ERR_OOM: return "device out of memory";
+    case AIRG_ERR_CUDA: return "CUDA runtime error";
+    case AIRG_ERR_UNSUPPORTED: return "product row exceeds the working-set limit";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Shared declarations of the AIRG CUDA library (sm_103a).  Device data layout:
+//   * CSR operators: int32 row pointers / columns, FP64 values, one allocation per array.
+//   * Every level's solve-phase vectors live in ONE nested buffer per role: level l's vector
+//     occupies [off_l, off_l + n_l) with off_{l+1} = off_l + n_f(l), because level l stores its
+//     unknowns F-points first and its C-points (= level l+1's unknowns, in level l+1's own F-then-C
+//     order) last.  Restriction, recursion and prolongation therefore never permute.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/airg.h"
+
+namespace airg {
+
+#define AIRG_TRY(expr)          \
+  do {                          \
+    int _rc = (expr);           \
+    if (_rc != AIRG_OK) return _rc; \
+  } while (0)
+
+inline int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return AIRG_OK;
+  if (e == cudaErrorMemoryAllocation) return AIRG_ERR_OOM;
+  return AIRG_ERR_CUDA;
+}
+#define CU_TRY(expr) AIRG_TRY(::airg::cuda_status(expr))
+#define KERNEL_CHECK() CU_TRY(cudaGetLastError())
+
+constexpr int kF = 1;  // CF marker values (device and export): 0 unassigned, 1 F, 2 C
+constexpr int kC = 2;
+
+// Library-owned device CSR.
+struct DCsr {
+  int nrows = 0, ncols = 0, nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* v = nullptr;
+};
+
+// Stream-ordered device memory with ownership tracking.  Everything allocated through an Arena
+// is released by release() (or the destructor of the owner that calls it).
+struct Arena {
+  cudaStream_t s = nullptr;
+  std::vector<void*> ptrs;
+  template <class T>
+  int alloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return e == cudaErrorMemoryAllocation ? AIRG_ERR_OOM : AIRG_ERR_CUDA;
+    }
+    ptrs.push_back((void*)*p);
+    return AIRG_OK;
+  }
+  int csr(DCsr& A, int nrows, int ncols, int nnz) {
+    A.nrows = nrows;
+    A.ncols = ncols;
+    A.nnz = nnz;
+    AIRG_TRY(alloc(&A.rp, (size_t)nrows + 1));
+    AIRG_TRY(alloc(&A.ci, (size_t)nnz));
+    AIRG_TRY(alloc(&A.v, (size_t)nnz));
+    return AIRG_OK;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+    ptrs.clear();
+  }
+};
+
+// Every kernel launch of the library is counted (airg_launch_count).
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int grid_for(long long work, int block, int cap = 152 * 32) {
+  long long g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------------------------------
+// Primitives (airg_prims.cu)
+// ------------------------------------------------------------------------------------------
+// Exclusive scan of n int32 values into out (n+1 entries, out[n] = total); total also returned
+// to *total_host when non-null (synchronises the stream).
+int scan_i32(const int* in, int* out, int n, Arena& tmp, cudaStream_t s, long long* total_host);
+int scan_i64(const long long* in, long long* out, int n, Arena& tmp, cudaStream_t s, long long* total_host);
+
+// Deterministic FP64 reductions: multi-column dot products and norms, two-stage with a fixed
+// grid and the final stage done by the last block to finish.
+struct Reducer {
+  double* partial = nullptr;  // [kRedBlocks * kRedCols]
+  unsigned* counter = nullptr;
+};
+constexpr int kRedBlocks = 304;
+constexpr int kRedCols = 34;
+int reducer_init(Reducer& r, Arena& a, cudaStream_t s);
+
+// out[0] = x.x (n entries)
+int dev_nrm2sq(const double* x, int n, double* out, Reducer& r, cudaStream_t s);
+
+// Gram-Schmidt pass over the first ncols columns of V (column-major, leading dim ldv):
+//   if hsub: w -= V hsub;   then dots[k] = V_k . w (k < ncols) and, if nrm, nrm[0] = w . w.
+int dev_gs_pass(const double* V, long long ldv, int ncols, double* w, int n, const double* hsub, double* dots,
+                double* nrm, Reducer& r, cudaStream_t s);
+
+// x += V y (first ncols columns)
+int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, double* x, int n, cudaStream_t s);
+
+// SpMV epilogues
+enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_ADDB = 3 };
+// y = A x (SET) | b - A x (RESID) | y + A x (ADD) | b + A x (ADDB; y may alias b)
+int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s);
+int pick_lanes(double avg_row_len);
+
+void dev_scale(const double* x, double alpha_div, double* y, int n, cudaStream_t s);  // y = x / a
+void dev_permute(const double* in, const int* pos, double* out, int n, bool inverse, cudaStream_t s);
+void dev_gather_prolong(double* x, int nf, const int* w, cudaStream_t s);  // x[f] = x[nf + w[f]]
+void dev_fill(double* x, double v, int n, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Setup (airg_setup.cu)
+// ------------------------------------------------------------------------------------------
+struct SetupParams {
+  double strong_threshold, ddc_fraction, drop_R, drop_Ac;
+  int pmisr_max_loops, poly_order, coarse_poly_order, coarse_iters, coarse_size, max_levels, n_smooth_up;
+  uint64_t seed;
+};
+
+// CF splitting of A (natural numbering); cf: device int8 n (1 F, 2 C).  strong (device uint8 nnz)
+// receives the strength flags when non-null.  nf_out: number of F-points.
+int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t* strong, int* nf_out,
+             Arena& tmp, cudaStream_t s);
+
+// GMRES polynomial coefficients of A (m coefficients) from the Box-Muller rhs of (seed, level).
+// alpha: device m doubles; fitted: host.
+int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int* fitted, Arena& tmp,
+             cudaStream_t s);
+
+// First-order fixed-sparsity approximate inverse on the pattern of A (diagonal required).
+int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out, Arena& own, Arena& tmp,
+                           cudaStream_t s);
+
+// C = scale * (A B) with the relative row-wise inf-norm drop (|c| < tol max|c_i.| dropped; the
+// diagonal kept when keep_diag).
+int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_diag, DCsr& out, Arena& own,
+           Arena& tmp, cudaStream_t s);
+
+struct LevelBuild {
+  // natural-numbering setup data of one level (owned by `own`)
+  DCsr A;            // level matrix
+  int n = 0, nf = 0, nc = 0;
+  int8_t* cf = nullptr;
+  int* pos = nullptr;   // natural index -> F-then-C position
+  int* Fnat = nullptr;  // F index -> natural
+  int* Cnat = nullptr;  // C index -> natural
+  DCsr Aff, Afc, Acf, Ainv, Z;
+  int* w = nullptr;     // F index -> C index (natural C numbering), -1 none
+  double* alpha = nullptr;
+  int m = 0, fitted = 0;
+  bool coarsest = false;
+};
+
+// Builds level data and the next coarse matrix (setup steps 1-11).  If the level turns out to be
+// the coarsest, only the polynomial is built and *Ac_out is left empty.
+int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coarsest, LevelBuild& L,
+                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s);
+
+// Nested solve numbering of a non-coarsest level from its F/C positions and the next level's
+// nested numbering (nullptr when the next level is the coarsest: identity there).
+int compose_layout(const LevelBuild& L, const int* lay_next, int* lay, cudaStream_t s);
+// Solve-phase operators of level l given level l+1's nested numbering (nullptr: identity).
+int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, Arena& own,
+                    Arena& tmp, cudaStream_t s);
+// Symmetric permutation of A by pos: row pos[i] gets row i with columns pos[j].
+int permute_matrix(const DCsr& A, const int* pos, DCsr& out, Arena& own, Arena& tmp, cudaStream_t s);
+
+// Input validation: sorted unique in-range columns, nonzero diagonal.
+int validate_csr(const DCsr& A, Arena& tmp, cudaStream_t s);
+
+}  // namespace airg

@@ -1,0 +1,76 @@
+// The hierarchy object behind the opaque airg_hierarchy handle.
+#pragma once
+#include <vector>
+
+#include "airg_common.cuh"
+
+namespace airg {
+
+// Solve-phase data of one level, in the level's F-then-C numbering.
+struct SolveLevel {
+  int n = 0, nf = 0, nc = 0;
+  long long off = 0;  // offset of this level's vector in the nested work buffers
+  bool coarsest = false;
+  DCsr AF;    // [A_ff A_fc] rows of the F-points, columns in F-then-C numbering (n_f x n)
+  DCsr Ainv;  // Ainv_ff (n_f x n_f); on the coarsest level the whole-matrix polynomial
+  DCsr Z;     // restrictor rows in the next level's numbering (n_c x n_f)
+  int* w = nullptr;  // one-point prolongation source per F-point (next level's numbering)
+  int* lay = nullptr;  // natural index of this level -> nested solve position (non-coarsest)
+  DCsr A;     // coarsest level only: the level matrix
+  int lanes_AF = 4, lanes_Ainv = 4, lanes_Z = 4, lanes_A = 4;
+  double bytes_AF = 0, bytes_Ainv = 0, bytes_Z = 0, bytes_A = 0;  // algorithmic bytes per SpMV
+};
+
+enum ProfClass { PC_SMOOTH_RESID = 0, PC_SMOOTH_UPDATE, PC_RESTRICT, PC_TOP_OP, PC_COARSEST, PC_PROLONG, PC_GS, PC_N };
+
+struct Profiler {
+  bool on = false;
+  unsigned mask = 0;  // bit c: time class c
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> pending;
+  long long launches[PC_N] = {};
+  double ms[PC_N] = {};
+  double bytes[PC_N] = {};
+};
+
+}  // namespace airg
+
+struct airg_hierarchy {
+  airg_params p{};
+  cudaStream_t s = nullptr;
+  airg::Arena solve_mem;  // solve-phase operators and workspaces
+  airg::Arena setup_mem;  // natural-numbering setup operators (released unless keep_setup)
+  std::vector<airg::LevelBuild> lb;
+  std::vector<std::vector<double>> alphas;  // host copies of each level's coefficients
+  std::vector<airg::SolveLevel> lv;
+  int n0 = 0;
+  airg::DCsr A0s;  // top-level matrix in level-0 F-then-C numbering
+  int* pos0 = nullptr;  // natural -> solve numbering (nullptr: identity)
+  int lanes_A0 = 4;
+  double bytes_A0 = 0;
+  // workspaces (allocated on first solve)
+  int restart_alloc = 0;
+  double *V = nullptr, *Zk = nullptr, *w = nullptr, *r = nullptr, *bwork = nullptr, *rtmp = nullptr,
+         *bp = nullptr, *xp = nullptr, *dsc = nullptr, *hb = nullptr, *hx = nullptr;
+  double* hsc = nullptr;  // pinned host mirror of dsc
+  airg::Reducer red{};
+  airg::Profiler prof;
+  // info
+  double setup_ms = 0, grid_cx = 0, op_cx = 0, storage_cx = 0;
+  long long top_nnz = 0;
+  bool kept = false;
+};
+
+namespace airg {
+int solve_alloc(airg_hierarchy* H, int restart);
+int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0);
+int solve_fgmres(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
+int solve_richardson(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
+int prof_flush(airg_hierarchy* H);
+}  // namespace airg

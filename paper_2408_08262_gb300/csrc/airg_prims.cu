@@ -1,0 +1,374 @@
+// Primitive kernels: scans, deterministic FP64 reductions, CSR SpMV with fused epilogues,
+// Gram-Schmidt passes and small vector kernels.  All of them are bandwidth-bound; none uses tensor
+// cores (nothing here is a dense contraction).
+#include "airg_common.cuh"
+
+namespace airg {
+
+// ------------------------------------------------------------------------------------------
+// Block-level helpers
+// ------------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Exclusive scan across a block of blockDim.x (multiple of 32, <= 1024) threads.
+template <class T>
+__device__ T block_excl_scan(T v, T* total) {
+  __shared__ T wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T t = lane < nw ? wsum[lane] : T(0);
+    T ti = warp_incl_scan(t);
+    if (lane < nw) wsum[lane] = ti - t;
+    if (lane == nw - 1 && total) *total = ti;
+  }
+  __syncthreads();
+  T r = inc - v + wsum[wid];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Exclusive scan (three kernels: tile sums, recursive scan of tile sums, tile scans)
+// ------------------------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__global__ void k_tile_sum(const T* __restrict__ in, T* __restrict__ tsum, int n) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  T s = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += blockDim.x) {
+    long long g = base + i;
+    if (g < n) s += in[g];
+  }
+  __shared__ T tot;
+  T ex = block_excl_scan<T>(s, &tot);
+  (void)ex;
+  __syncthreads();
+  if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void k_tile_scan(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ toff, int n) {
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T loc = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    long long g = base + j;
+    v[j] = g < n ? in[g] : T(0);
+    loc += v[j];
+  }
+  T run = block_excl_scan<T>(loc, (T*)nullptr) + (toff ? toff[blockIdx.x] : T(0));
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    long long g = base + j;
+    if (g < n) out[g] = run;
+    run += v[j];
+    if (g == n - 1) out[n] = run;
+  }
+}
+
+template <class T>
+static int scan_impl(const T* in, T* out, int n, Arena& tmp, cudaStream_t s, long long* total_host) {
+  if (n <= 0) {
+    CU_TRY(cudaMemsetAsync(out, 0, sizeof(T), s));
+    if (total_host) *total_host = 0;
+    return AIRG_OK;
+  }
+  int nt = ceil_div(n, kScanTile);
+  T* toff = nullptr;
+  if (nt > 1) {
+    T* tsum = nullptr;
+    AIRG_TRY(tmp.alloc(&tsum, nt));
+    AIRG_TRY(tmp.alloc(&toff, (size_t)nt + 1));
+    airg::note_launch(), k_tile_sum<T><<<nt, kScanThreads, 0, s>>>(in, tsum, n);
+    KERNEL_CHECK();
+    AIRG_TRY(scan_impl<T>(tsum, toff, nt, tmp, s, nullptr));
+  }
+  airg::note_launch(), k_tile_scan<T><<<nt, kScanThreads, 0, s>>>(in, out, toff, n);
+  KERNEL_CHECK();
+  if (total_host) {
+    T t = 0;
+    CU_TRY(cudaMemcpyAsync(&t, out + n, sizeof(T), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    *total_host = (long long)t;
+  }
+  return AIRG_OK;
+}
+
+int scan_i32(const int* in, int* out, int n, Arena& tmp, cudaStream_t s, long long* total_host) {
+  return scan_impl<int>(in, out, n, tmp, s, total_host);
+}
+int scan_i64(const long long* in, long long* out, int n, Arena& tmp, cudaStream_t s, long long* total_host) {
+  return scan_impl<long long>(in, out, n, tmp, s, total_host);
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic reductions
+// ------------------------------------------------------------------------------------------
+int reducer_init(Reducer& r, Arena& a, cudaStream_t s) {
+  AIRG_TRY(a.alloc(&r.partial, (size_t)kRedBlocks * kRedCols));
+  AIRG_TRY(a.alloc(&r.counter, 1));
+  CU_TRY(cudaMemsetAsync(r.counter, 0, sizeof(unsigned), s));
+  return AIRG_OK;
+}
+
+// Reduces acc[0..nv) across the block, writes the block's partials, and lets the last block to
+// finish sum all partials in block order into out[0..nv).  Fixed grid => deterministic.
+template <int NV>
+__device__ void block_partials_finish(const double (&acc)[NV], int nv, double* partial, unsigned* counter,
+                                      double* out0, int nout0, double* out1) {
+  __shared__ double red[8][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    if (k < nv) {
+      double t = warp_sum(acc[k]);
+      if (lane == 0) red[wid][k] = t;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w][k];
+    partial[(size_t)blockIdx.x * kRedCols + k] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)partial)[(size_t)b * kRedCols + k];
+    if (k < nout0) {
+      if (out0) out0[k] = t;
+    } else if (out1) {
+      out1[0] = t;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_nrm2sq(const double* __restrict__ x, int n, double* out,
+                                                double* partial, unsigned* counter) {
+  double acc[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double t = x[i];
+    acc[0] += t * t;
+  }
+  block_partials_finish<1>(acc, 1, partial, counter, out, 1, nullptr);
+}
+
+int dev_nrm2sq(const double* x, int n, double* out, Reducer& r, cudaStream_t s) {
+  airg::note_launch(), k_nrm2sq<<<kRedBlocks, 256, 0, s>>>(x, n, out, r.partial, r.counter);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_gs_pass(const double* __restrict__ V, long long ldv, int ncols,
+                                                 double* __restrict__ w, int n, const double* __restrict__ hsub,
+                                                 double* dots, double* nrm, double* partial, unsigned* counter) {
+  __shared__ double sh[NC];
+  if (hsub)
+    for (int k = threadIdx.x; k < ncols; k += blockDim.x) sh[k] = hsub[k];
+  __syncthreads();
+  const int nd = dots ? ncols : 0;  // dot products wanted
+  double acc[NC + 1];
+#pragma unroll
+  for (int k = 0; k <= NC; ++k) acc[k] = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double wr = w[r];
+    if (hsub) {
+      double sub = 0.0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k)
+        if (k < ncols) sub += V[(size_t)k * ldv + r] * sh[k];
+      wr -= sub;
+      w[r] = wr;
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      if (k < nd) acc[k] += V[(size_t)k * ldv + r] * wr;
+    acc[NC] += wr * wr;
+  }
+  // place the norm accumulator right after the nd dots so one finish call reduces nd+1 values
+#pragma unroll
+  for (int k = 0; k < NC; ++k)
+    if (k == nd) acc[k] = acc[NC];
+  block_partials_finish<NC + 1>(acc, nd + 1, partial, counter, dots, nd, nrm);
+}
+
+int dev_gs_pass(const double* V, long long ldv, int ncols, double* w, int n, const double* hsub, double* dots,
+                double* nrm, Reducer& r, cudaStream_t s) {
+  if (ncols < 1 || ncols > 32) return AIRG_ERR_ARG;
+  if (ncols <= 4)
+    airg::note_launch(), k_gs_pass<4><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
+  else if (ncols <= 8)
+    airg::note_launch(), k_gs_pass<8><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
+  else if (ncols <= 16)
+    airg::note_launch(), k_gs_pass<16><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
+  else
+    airg::note_launch(), k_gs_pass<32><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+__global__ void k_multi_axpy(const double* __restrict__ V, long long ldv, int ncols, const double* __restrict__ y,
+                             double* __restrict__ x, int n) {
+  __shared__ double sy[64];
+  for (int k = threadIdx.x; k < ncols; k += blockDim.x) sy[k] = y[k];
+  __syncthreads();
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double t = x[r];
+    for (int k = 0; k < ncols; ++k) t += sy[k] * V[(size_t)k * ldv + r];
+    x[r] = t;
+  }
+}
+
+int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, double* x, int n, cudaStream_t s) {
+  if (ncols <= 0) return AIRG_OK;
+  if (ncols > 64) return AIRG_ERR_ARG;
+  airg::note_launch(), k_multi_axpy<<<grid_for(n, 256), 256, 0, s>>>(V, ldv, ncols, y, x, n);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// CSR SpMV: LPR lanes cooperate on one row; the epilogue is fused.
+// ------------------------------------------------------------------------------------------
+template <int LPR, int MODE>
+__global__ void __launch_bounds__(256) k_spmv(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const double* __restrict__ v, const double* __restrict__ x,
+                                              const double* b, double* y) {
+  // The loop bound is uniform across the warp (every lane iterates the same number of times), so
+  // the width-LPR shuffles always run with the whole warp present.
+  constexpr int GPW = 32 / LPR;  // row groups per warp
+  const int lane = threadIdx.x % LPR;
+  const int gin = (threadIdx.x & 31) / LPR;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * GPW; base < nrows; base += nwarps * GPW) {
+    const long long row = base + gin;
+    const bool valid = row < nrows;
+    double s = 0.0;
+    if (valid) {
+      const int beg = rp[row], end = rp[row + 1];
+      for (int k = beg + lane; k < end; k += LPR) s += v[k] * __ldg(x + ci[k]);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (valid && lane == 0) {
+      double out;
+      if (MODE == SPMV_SET) out = s;
+      else if (MODE == SPMV_RESID) out = b[row] - s;
+      else if (MODE == SPMV_ADD) out = y[row] + s;
+      else out = b[row] + s;
+      y[row] = out;
+    }
+  }
+}
+
+int pick_lanes(double L) {
+  if (L <= 3.0) return 2;
+  if (L <= 7.0) return 4;
+  if (L <= 14.0) return 8;
+  if (L <= 28.0) return 16;
+  return 32;
+}
+
+template <int LPR>
+static void launch_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
+  const int block = 256;
+  long long work = (long long)A.nrows * LPR;
+  int grid = grid_for(work, block, 152 * 16);
+  switch (mode) {
+    case SPMV_SET: airg::note_launch(), k_spmv<LPR, SPMV_SET><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv<LPR, SPMV_RESID><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv<LPR, SPMV_ADD><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
+    default: airg::note_launch(), k_spmv<LPR, SPMV_ADDB><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
+  }
+}
+
+int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
+  if (A.nrows <= 0) return AIRG_OK;
+  switch (lanes) {
+    case 1: launch_spmv<1>(A, x, b, y, mode, s); break;
+    case 2: launch_spmv<2>(A, x, b, y, mode, s); break;
+    case 4: launch_spmv<4>(A, x, b, y, mode, s); break;
+    case 8: launch_spmv<8>(A, x, b, y, mode, s); break;
+    case 16: launch_spmv<16>(A, x, b, y, mode, s); break;
+    default: launch_spmv<32>(A, x, b, y, mode, s); break;
+  }
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Small vector kernels
+// ------------------------------------------------------------------------------------------
+__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] / a;
+}
+void dev_scale(const double* x, double a, double* y, int n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_scale<<<grid_for(n, 256), 256, 0, s>>>(x, a, y, n);
+}
+
+__global__ void k_permute(const double* __restrict__ in, const int* __restrict__ pos, double* __restrict__ out, int n,
+                          bool inverse) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (inverse) out[i] = in[pos[i]];
+    else out[pos[i]] = in[i];
+  }
+}
+void dev_permute(const double* in, const int* pos, double* out, int n, bool inverse, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_permute<<<grid_for(n, 256), 256, 0, s>>>(in, pos, out, n, inverse);
+}
+
+__global__ void k_gather_prolong(double* x, int nf, const int* __restrict__ w) {
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    int c = w[f];
+    x[f] = c >= 0 ? x[nf + c] : 0.0;
+  }
+}
+void dev_gather_prolong(double* x, int nf, const int* w, cudaStream_t s) {
+  if (nf > 0) airg::note_launch(), k_gather_prolong<<<grid_for(nf, 256), 256, 0, s>>>(x, nf, w);
+}
+
+__global__ void k_fill(double* x, double v, int n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+void dev_fill(double* x, double v, int n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_fill<<<grid_for(n, 256), 256, 0, s>>>(x, v, n);
+}
+
+}  // namespace airg

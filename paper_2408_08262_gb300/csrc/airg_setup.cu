@@ -1,0 +1,1229 @@
+// AIRG setup on the GPU: every step of Section "AIRG" (setup steps 1-11) as CUDA kernels.
+//
+//   step 1  CF splitting ........ strength (eq. soc), PMISR (Algorithm 1), DDC (Algorithm 2)
+//   step 2  extraction .......... stable F/C renumbering by prefix sums, A_ff / A_fc / A_cf
+//   steps 3-6 polynomial fit .... Box-Muller rhs, power basis by SpMV, Householder TSQR, Givens LSQ
+//   steps 7-8 approximate inverse first-order fixed-sparsity powers, assembled Ainv
+//   step 9  restrictor .......... Z = -A_cf Ainv with the relative row-wise inf-norm drop
+//   step 10 prolongator ......... classical one-point map (weight 1)
+//   step 11 coarse matrix ....... A_c = R (A P) with drop, diagonal kept
+//
+// Integer decisions (strength flags, PMISR, DDC, patterns, drops) and the product values are
+// computed in a fixed arithmetic order (ascending index, explicit fma) so that, given the same
+// input matrix and coefficients, they reproduce the plain definitions bit for bit.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "airg_common.cuh"
+
+namespace airg {
+
+// ------------------------------------------------------------------------------------------
+// Counter-based random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014).  Output c of a
+// stream keyed by K is mix(K + (c+1) * gamma); keys are derived from (seed, level, stream).
+// ------------------------------------------------------------------------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// stream 0: PMISR tie-break weights, stream 1: Box-Muller right-hand side
+__host__ __device__ __forceinline__ uint64_t sm64_key(uint64_t seed, int level, int stream) {
+  return sm64_mix(seed + kGamma * (uint64_t)(1 + 2 * level + stream));
+}
+__device__ __forceinline__ double sm64_unif(uint64_t key, uint64_t c) {
+  return (double)(sm64_mix(key + kGamma * (c + 1)) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+#define GRID(n) grid_for((n), 256), 256, 0, s
+
+// ------------------------------------------------------------------------------------------
+// Input validation
+// ------------------------------------------------------------------------------------------
+__global__ void k_validate(int n, int nnz, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ v, int* flags) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int b = rp[i], e = rp[i + 1];
+    if (b < 0 || e < b || e > nnz) { atomicOr(flags, 1); continue; }
+    bool diag = false;
+    for (int k = b; k < e; ++k) {
+      int j = ci[k];
+      if (j < 0 || j >= n || (k > b && j <= ci[k - 1])) atomicOr(flags, 1);
+      if (j == i) diag = (v[k] != 0.0);
+    }
+    if (!diag) atomicOr(flags, 2);
+  }
+}
+
+int validate_csr(const DCsr& A, Arena& tmp, cudaStream_t s) {
+  int* flags;
+  AIRG_TRY(tmp.alloc(&flags, 1));
+  CU_TRY(cudaMemsetAsync(flags, 0, sizeof(int), s));
+  int ends[2] = {0, 0};
+  CU_TRY(cudaMemcpyAsync(&ends[0], A.rp, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaMemcpyAsync(&ends[1], A.rp + A.nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (A.nrows > 0) airg::note_launch(), k_validate<<<GRID(A.nrows)>>>(A.nrows, A.nnz, A.rp, A.ci, A.v, flags);
+  KERNEL_CHECK();
+  int h = 0;
+  CU_TRY(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  if (ends[0] != 0 || ends[1] != A.nnz || (h & 1)) return AIRG_ERR_CSR;
+  if (h & 2) return AIRG_ERR_ZERO_DIAG;
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Step 1a: strength of connection, eq. soc with absolute values.  strong(i,j) iff j != i,
+// a_ij != 0 and |a_ij| >= alpha * max_{k != i} |a_ik|; a row with zero off-diagonal maximum has
+// no strong entry.  nS[i] = |S_i|.
+// ------------------------------------------------------------------------------------------
+__global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                           double alpha, uint8_t* __restrict__ strong, int* __restrict__ nS) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int b = rp[i], e = rp[i + 1];
+    double mx = 0.0;
+    for (int k = b; k < e; ++k)
+      if (ci[k] != i) mx = fmax(mx, fabs(v[k]));
+    const double thr = alpha * mx;
+    int cnt = 0;
+    for (int k = b; k < e; ++k) {
+      const double a = v[k];
+      const bool st = (mx != 0.0) && (ci[k] != i) && (a != 0.0) && (fabs(a) >= thr);
+      strong[k] = st;
+      cnt += st;
+    }
+    nS[i] = cnt;
+  }
+}
+
+// |S_i^T| and the transpose adjacency (order within a row is irrelevant: it is used as a set)
+__global__ void k_strong_T_count(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                 const uint8_t* __restrict__ strong, int* nST) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (strong[k]) atomicAdd(nST + ci[k], 1);
+}
+__global__ void k_strong_T_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const uint8_t* __restrict__ strong, const int* __restrict__ rpT, int* cursor,
+                                int* __restrict__ colT) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (strong[k]) {
+        int j = ci[k];
+        int p = atomicAdd(cursor + j, 1);
+        colT[rpT[j] + p] = (int)i;
+      }
+}
+
+// ------------------------------------------------------------------------------------------
+// Step 1b: PMISR, Algorithm 1.  w_i = |S_i| + |S_i^T| + r_i; {w < 1} (isolated nodes) start as F.
+// Each round: D = unassigned nodes whose (w, index) is smaller than that of every unassigned
+// neighbour in S_i u S_i^T (state frozen at the round start); D -> F, unassigned neighbours of D
+// -> C.  After n_loops^max rounds the remaining nodes become C.
+// ------------------------------------------------------------------------------------------
+__global__ void k_pmisr_init(int n, const int* __restrict__ nS, const int* __restrict__ nST, uint64_t key,
+                             double* __restrict__ w, int8_t* __restrict__ cf) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int deg = nS[i] + nST[i];
+    const double wi = (double)deg + sm64_unif(key, (uint64_t)i);
+    w[i] = wi;
+    cf[i] = (wi < 1.0) ? (int8_t)kF : (int8_t)0;
+  }
+}
+
+__device__ __forceinline__ bool pmisr_less(double wi, int i, double wj, int j) {
+  return wi < wj || (wi == wj && i < j);
+}
+
+__global__ void k_pmisr_select(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const uint8_t* __restrict__ strong, const int* __restrict__ rpT,
+                               const int* __restrict__ colT, const double* __restrict__ w,
+                               const int8_t* __restrict__ cf, uint8_t* __restrict__ D) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    uint8_t isD = 0;
+    if (cf[i] == 0) {
+      const double wi = w[i];
+      bool mn = true;
+      for (int k = rp[i]; k < rp[i + 1] && mn; ++k) {
+        if (!strong[k]) continue;
+        const int j = ci[k];
+        if (cf[j] == 0 && !pmisr_less(wi, i, w[j], j)) mn = false;
+      }
+      for (int k = rpT[i]; k < rpT[i + 1] && mn; ++k) {
+        const int j = colT[k];
+        if (cf[j] == 0 && !pmisr_less(wi, i, w[j], j)) mn = false;
+      }
+      isD = mn;
+    }
+    D[i] = isD;
+  }
+}
+
+__global__ void k_pmisr_apply(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const uint8_t* __restrict__ strong, const int* __restrict__ rpT,
+                              const int* __restrict__ colT, const uint8_t* __restrict__ D, int8_t* __restrict__ cf,
+                              int* n_unassigned) {
+  int left = 0;
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    if (cf[i] != 0) continue;
+    if (D[i]) { cf[i] = kF; continue; }
+    bool nbD = false;
+    for (int k = rp[i]; k < rp[i + 1] && !nbD; ++k)
+      if (strong[k] && D[ci[k]]) nbD = true;
+    for (int k = rpT[i]; k < rpT[i + 1] && !nbD; ++k)
+      if (D[colT[k]]) nbD = true;
+    if (nbD) cf[i] = kC;
+    else left++;
+  }
+  if (left) atomicAdd(n_unassigned, left);
+}
+
+__global__ void k_pmisr_finalize(int n, int8_t* cf) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (cf[i] == 0) cf[i] = kC;
+}
+
+// ------------------------------------------------------------------------------------------
+// Step 1c: DDC, Algorithm 2.  theta_i = sum_{j in F, j != i} |a_ij| / |a_ii| (ascending column
+// order; +inf for a zero diagonal with a nonzero sum).  Candidates: F with theta != 0.
+// k = floor(fraction |F|) capped by the candidates; tau = k-th largest candidate theta (exact
+// radix select on the bit patterns of the positive doubles); candidates with theta >= tau -> C.
+// ------------------------------------------------------------------------------------------
+__global__ void k_ddc_theta(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                            const int8_t* __restrict__ cf, double* __restrict__ theta, int* counts) {
+  int nf = 0, nc = 0;
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    double th = 0.0;
+    if (cf[i] == kF) {
+      double sum = 0.0, d = 0.0;
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j == i) d = fabs(v[k]);
+        else if (cf[j] == kF) sum += fabs(v[k]);
+      }
+      th = (sum == 0.0) ? 0.0 : sum / d;
+      nf++;
+      nc += (th != 0.0);
+    }
+    theta[i] = th;
+  }
+  if (nf) atomicAdd(counts, nf);
+  if (nc) atomicAdd(counts + 1, nc);
+}
+
+struct RadixState {
+  unsigned long long prefix, mask;
+  long long krem;
+};
+
+__global__ void k_radix_hist(int n, const int8_t* __restrict__ cf, const double* __restrict__ theta,
+                             const RadixState* st, int shift, unsigned* hist) {
+  __shared__ unsigned sh[256];
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) sh[t] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double th = theta[i];
+    if (cf[i] != kF || th == 0.0) continue;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(th);
+    if ((bits & mask) == prefix) atomicAdd(&sh[(bits >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 256; t += blockDim.x)
+    if (sh[t]) atomicAdd(hist + t, sh[t]);
+}
+
+__global__ void k_radix_pick(RadixState* st, int shift, unsigned* hist) {
+  if (threadIdx.x == 0) {
+    long long cum = 0;
+    int d = 0;
+    for (d = 255; d >= 0; --d) {
+      if (cum + (long long)hist[d] >= st->krem) break;
+      cum += hist[d];
+    }
+    if (d < 0) d = 0;
+    st->krem -= cum;
+    st->prefix |= ((unsigned long long)d) << shift;
+    st->mask |= 255ULL << shift;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+}
+
+__global__ void k_ddc_apply(int n, int8_t* __restrict__ cf, const double* __restrict__ theta, const RadixState* st,
+                            int* converted) {
+  const double tau = __longlong_as_double((long long)st->prefix);
+  int cnt = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double th = theta[i];
+    if (cf[i] == kF && th != 0.0 && th >= tau) { cf[i] = kC; cnt++; }
+  }
+  if (cnt) atomicAdd(converted, cnt);
+}
+
+int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t* strong_out, int* nf_out,
+             Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  if (n == 0) { *nf_out = 0; return AIRG_OK; }
+  uint8_t* strong = strong_out;
+  if (!strong) AIRG_TRY(tmp.alloc(&strong, A.nnz));
+  int *nS, *nST, *rpT, *cursor, *colT, *ctr;
+  AIRG_TRY(tmp.alloc(&nS, n));
+  AIRG_TRY(tmp.alloc(&nST, n));
+  AIRG_TRY(tmp.alloc(&rpT, (size_t)n + 1));
+  AIRG_TRY(tmp.alloc(&cursor, n));
+  AIRG_TRY(tmp.alloc(&ctr, 4));
+  CU_TRY(cudaMemsetAsync(nST, 0, sizeof(int) * n, s));
+  CU_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * n, s));
+  CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * 4, s));
+  airg::note_launch(), k_strength<<<GRID(n)>>>(n, A.rp, A.ci, A.v, p.strong_threshold, strong, nS);
+  airg::note_launch(), k_strong_T_count<<<GRID(n)>>>(n, A.rp, A.ci, strong, nST);
+  KERNEL_CHECK();
+  long long nT = 0;
+  AIRG_TRY(scan_i32(nST, rpT, n, tmp, s, &nT));
+  AIRG_TRY(tmp.alloc(&colT, (size_t)nT));
+  airg::note_launch(), k_strong_T_fill<<<GRID(n)>>>(n, A.rp, A.ci, strong, rpT, cursor, colT);
+  double* w;
+  uint8_t* D;
+  AIRG_TRY(tmp.alloc(&w, n));
+  AIRG_TRY(tmp.alloc(&D, n));
+  airg::note_launch(), k_pmisr_init<<<GRID(n)>>>(n, nS, nST, sm64_key(p.seed, level, 0), w, cf);
+  KERNEL_CHECK();
+  for (int loop = 1;; ++loop) {
+    if (p.pmisr_max_loops > 0 && loop > p.pmisr_max_loops) break;
+    CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(int), s));
+    airg::note_launch(), k_pmisr_select<<<GRID(n)>>>(n, A.rp, A.ci, strong, rpT, colT, w, cf, D);
+    airg::note_launch(), k_pmisr_apply<<<GRID(n)>>>(n, A.rp, A.ci, strong, rpT, colT, D, cf, ctr);
+    KERNEL_CHECK();
+    if (p.pmisr_max_loops <= 0) {  // uncapped: loop until nothing is left
+      int left = 0;
+      CU_TRY(cudaMemcpyAsync(&left, ctr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU_TRY(cudaStreamSynchronize(s));
+      if (left == 0) break;
+    }
+  }
+  airg::note_launch(), k_pmisr_finalize<<<GRID(n)>>>(n, cf);
+  // DDC
+  double* theta;
+  AIRG_TRY(tmp.alloc(&theta, n));
+  CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * 4, s));
+  airg::note_launch(), k_ddc_theta<<<GRID(n)>>>(n, A.rp, A.ci, A.v, cf, theta, ctr);
+  KERNEL_CHECK();
+  int hc[2];
+  CU_TRY(cudaMemcpyAsync(hc, ctr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  const long long nF = hc[0], ncand = hc[1];
+  long long k = (long long)std::floor(p.ddc_fraction * (double)nF);
+  k = std::min(k, ncand);
+  int converted = 0;
+  if (k > 0) {
+    RadixState* st;
+    unsigned* hist;
+    AIRG_TRY(tmp.alloc(&st, 1));
+    AIRG_TRY(tmp.alloc(&hist, 256));
+    RadixState h0{0ULL, 0ULL, k};
+    CU_TRY(cudaMemcpyAsync(st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
+    CU_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), s));
+    for (int pass = 0; pass < 8; ++pass) {
+      const int shift = 56 - 8 * pass;
+      airg::note_launch(), k_radix_hist<<<GRID(n)>>>(n, cf, theta, st, shift, hist);
+      airg::note_launch(), k_radix_pick<<<1, 256, 0, s>>>(st, shift, hist);
+    }
+    airg::note_launch(), k_ddc_apply<<<GRID(n)>>>(n, cf, theta, st, ctr + 2);
+    KERNEL_CHECK();
+    CU_TRY(cudaMemcpyAsync(&converted, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+  }
+  *nf_out = (int)(nF - converted);
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Step 2: stable F/C renumbering and block extraction
+// ------------------------------------------------------------------------------------------
+__global__ void k_isF(int n, const int8_t* __restrict__ cf, int* __restrict__ f) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    f[i] = cf[i] == kF;
+}
+// fpos: exclusive scan of isF.  pos(i) = F ? fpos(i) : nf + (i - fpos(i)).
+__global__ void k_cf_maps(int n, int nf, const int8_t* __restrict__ cf, const int* __restrict__ fpos, int* __restrict__ pos,
+                          int* __restrict__ Fnat, int* __restrict__ Cnat) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    const int fp = fpos[i];
+    if (cf[i] == kF) { pos[i] = fp; Fnat[fp] = i; }
+    else { pos[i] = nf + (i - fp); Cnat[i - fp] = i; }
+  }
+}
+__global__ void k_extract_count(int n, const int* __restrict__ rp, const int* __restrict__ ci, const int8_t* __restrict__ cf,
+                                const int* __restrict__ fpos, int* __restrict__ cFF, int* __restrict__ cFC,
+                                int* __restrict__ cCF) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    int nFcol = 0, nCcol = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (cf[ci[k]] == kF) nFcol++;
+      else nCcol++;
+    }
+    const int fp = fpos[i];
+    if (cf[i] == kF) { cFF[fp] = nFcol; cFC[fp] = nCcol; }
+    else cCF[i - fp] = nFcol;
+  }
+}
+__global__ void k_extract_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                               const int8_t* __restrict__ cf, const int* __restrict__ fpos, DCsr Aff, DCsr Afc, DCsr Acf) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    const int fp = fpos[i];
+    if (cf[i] == kF) {
+      int a = Aff.rp[fp], b = Afc.rp[fp];
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        const int fj = fpos[j];
+        if (cf[j] == kF) { Aff.ci[a] = fj; Aff.v[a++] = v[k]; }
+        else { Afc.ci[b] = j - fj; Afc.v[b++] = v[k]; }
+      }
+    } else {
+      int a = Acf.rp[i - fp];
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (cf[j] == kF) { Acf.ci[a] = fpos[j]; Acf.v[a++] = v[k]; }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Steps 3-6: GMRES polynomial coefficients
+// ------------------------------------------------------------------------------------------
+// Box-Muller: entry i uses u1 = 1 - r(2i), u2 = r(2i+1): z = sqrt(-2 ln u1) cos(2 pi u2).
+__global__ void k_box_muller(int n, uint64_t key, double* __restrict__ z) {
+  const double two_pi = 6.283185307179586;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double u1 = 1.0 - sm64_unif(key, 2 * (uint64_t)i);
+    const double u2 = sm64_unif(key, 2 * (uint64_t)i + 1);
+    z[i] = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+  }
+}
+
+// Householder QR of a tall block held in shared memory (column-major [nc][kQrRows]).  Rows of
+// block b are [b*rows_per_block, ...) of the input, element (r, c) at in[r*rs + c*cs].  The
+// upper-triangular nc x nc factor (row-major, zeros below the diagonal and in rows past the
+// block's row count) goes to out + b*nc*nc.  Used for the first TSQR stage (the power basis) and
+// for every combine stage (stacked R factors).
+constexpr int kQrRows = 256;
+constexpr int kQrMaxCols = 16;
+
+__global__ void __launch_bounds__(256) k_householder(const double* __restrict__ in, long long rs, long long cs,
+                                                     long long nrows, int nc, int rows_per_block,
+                                                     double* __restrict__ out) {
+  __shared__ double M[kQrMaxCols][kQrRows];
+  __shared__ double red[8][kQrMaxCols + 1];
+  __shared__ double tot[kQrMaxCols + 1];
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long rem = nrows - r0;
+  const int rows = (int)(rem < rows_per_block ? rem : rows_per_block);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < nc; ++c)
+    for (int r = threadIdx.x; r < kQrRows; r += blockDim.x)
+      M[c][r] = (r < rows) ? in[(r0 + r) * rs + (long long)c * cs] : 0.0;
+  __syncthreads();
+  const int kmax = rows < nc ? rows : nc;
+  for (int k = 0; k < kmax; ++k) {
+    // ||x||^2 of column k, rows k..rows-1
+    double p = 0.0;
+    for (int r = k + threadIdx.x; r < rows; r += blockDim.x) p += M[k][r] * M[k][r];
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) red[wid][0] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][0];
+      tot[0] = t;
+    }
+    __syncthreads();
+    const double xn = sqrt(tot[0]);
+    const double x0 = M[k][k];
+    const double a = (x0 >= 0.0) ? -xn : xn;
+    __syncthreads();
+    if (threadIdx.x == 0) M[k][k] = x0 - a;  // v = x - a e1 stored in column k
+    __syncthreads();
+    // dots v . M[:, j] for j = k..nc-1 (j = k gives ||v||^2)
+    double d[kQrMaxCols];
+#pragma unroll
+    for (int j = 0; j < kQrMaxCols; ++j) d[j] = 0.0;
+    for (int r = k + threadIdx.x; r < rows; r += blockDim.x) {
+      const double vr = M[k][r];
+#pragma unroll
+      for (int j = 0; j < kQrMaxCols; ++j)
+        if (j >= k && j < nc) d[j] += vr * M[j][r];
+    }
+#pragma unroll
+    for (int j = 0; j < kQrMaxCols; ++j) {
+      if (j >= k && j < nc) {
+        double t = d[j];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[wid][j] = t;
+      }
+    }
+    __syncthreads();
+    for (int j = k + threadIdx.x; j < nc; j += blockDim.x) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][j];
+      tot[j] = t;
+    }
+    __syncthreads();
+    const double vn2 = tot[k];
+    if (vn2 > 0.0) {
+      for (int j = k + 1; j < nc; ++j) {
+        const double sj = 2.0 * tot[j] / vn2;
+        for (int r = k + threadIdx.x; r < rows; r += blockDim.x) M[j][r] -= sj * M[k][r];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) M[k][k] = a;  // R(k,k); rows below k in column k are discarded
+    __syncthreads();
+  }
+  double* o = out + (size_t)blockIdx.x * nc * nc;
+  for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
+    const int r = t / nc, c = t % nc;
+    o[t] = (r <= c && r < kmax) ? M[c][r] : 0.0;
+  }
+}
+
+// Least squares min || beta e1 - R(:, 2:end) y || (setup step 6), breakdown truncation when
+// |R_cc| <= 1e-12 ||R(:,c)||, Givens rotations and back substitution.  One thread.
+__global__ void k_poly_lsq(const double* __restrict__ R, int m, double* __restrict__ alpha, int* fitted) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int nc = m + 1;
+  int mf = m;
+  for (int c = 1; c <= m; ++c) {
+    double cn = 0.0;
+    for (int r = 0; r <= c; ++r) cn += R[r * nc + c] * R[r * nc + c];
+    cn = sqrt(cn);
+    if (!(fabs(R[c * nc + c]) > 1e-12 * cn)) { mf = c; break; }
+  }
+  double H[kQrMaxCols + 1][kQrMaxCols];
+  double g[kQrMaxCols + 1];
+  for (int i = 0; i <= mf; ++i) {
+    g[i] = 0.0;
+    for (int j = 0; j < mf; ++j) H[i][j] = R[i * nc + j + 1];
+  }
+  g[0] = R[0];
+  for (int k = 0; k < mf; ++k) {
+    const double a = H[k][k], b = H[k + 1][k];
+    const double d = hypot(a, b);
+    double c_ = 1.0, s_ = 0.0;
+    if (d != 0.0) { c_ = a / d; s_ = b / d; }
+    for (int j = k; j < mf; ++j) {
+      const double t1 = H[k][j], t2 = H[k + 1][j];
+      H[k][j] = c_ * t1 + s_ * t2;
+      H[k + 1][j] = -s_ * t1 + c_ * t2;
+    }
+    const double t1 = g[k], t2 = g[k + 1];
+    g[k] = c_ * t1 + s_ * t2;
+    g[k + 1] = -s_ * t1 + c_ * t2;
+  }
+  for (int i = 0; i < m; ++i) alpha[i] = 0.0;
+  for (int i = mf - 1; i >= 0; --i) {
+    double sum = g[i];
+    for (int j = i + 1; j < mf; ++j) sum -= H[i][j] * alpha[j];
+    alpha[i] = (H[i][i] != 0.0) ? sum / H[i][i] : 0.0;
+  }
+  *fitted = mf;
+}
+
+int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int* fitted, Arena& tmp,
+             cudaStream_t s) {
+  const int n = A.nrows, nc = m + 1;
+  if (m < 1 || nc > kQrMaxCols) return AIRG_ERR_ARG;
+  if (n == 0) {
+    CU_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * m, s));
+    *fitted = 0;
+    return AIRG_OK;
+  }
+  double* K;
+  AIRG_TRY(tmp.alloc(&K, (size_t)n * nc));
+  airg::note_launch(), k_box_muller<<<GRID(n)>>>(n, sm64_key(seed, level, 1), K);
+  KERNEL_CHECK();
+  const int lanes = pick_lanes((double)A.nnz / std::max(1, n));
+  for (int c = 1; c < nc; ++c) AIRG_TRY(dev_spmv(A, K + (size_t)(c - 1) * n, nullptr, K + (size_t)c * n, SPMV_SET, lanes, s));
+  // TSQR: stage 1 on the power basis, then combine stacked factors until one remains
+  long long nb = (n + kQrRows - 1) / kQrRows;
+  double* R;
+  AIRG_TRY(tmp.alloc(&R, (size_t)nb * nc * nc));
+  airg::note_launch(), k_householder<<<(int)nb, 256, 0, s>>>(K, 1, n, n, nc, kQrRows, R);
+  KERNEL_CHECK();
+  const int group = std::max(1, kQrRows / nc);
+  while (nb > 1) {
+    long long nb2 = (nb + group - 1) / group;
+    double* R2;
+    AIRG_TRY(tmp.alloc(&R2, (size_t)nb2 * nc * nc));
+    airg::note_launch(), k_householder<<<(int)nb2, 256, 0, s>>>(R, nc, 1, nb * nc, nc, group * nc, R2);
+    KERNEL_CHECK();
+    R = R2;
+    nb = nb2;
+  }
+  int* dfit;
+  AIRG_TRY(tmp.alloc(&dfit, 1));
+  airg::note_launch(), k_poly_lsq<<<1, 32, 0, s>>>(R, m, alpha, dfit);
+  KERNEL_CHECK();
+  CU_TRY(cudaMemcpyAsync(fitted, dfit, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Steps 7-8: first-order fixed-sparsity powers (eq. fixed_sparsity), one thread per entry.
+//   P1 = A;  P_p(i,j) = sum_{l in S_i ascending} P_{p-1}(i,l) a_lj   (fma; l with no a_lj skipped)
+//   Ainv(i,j) = alpha_0 delta_ij + alpha_1 P1(i,j) + ... accumulated left to right with fma.
+// ------------------------------------------------------------------------------------------
+__global__ void k_row_index(int n, const int* __restrict__ rp, int* __restrict__ rowidx) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) rowidx[k] = (int)i;
+}
+
+__device__ __forceinline__ int find_col(const int* __restrict__ ci, int b, int e, int j) {
+  while (b < e) {
+    const int mid = (b + e) >> 1;
+    const int c = ci[mid];
+    if (c < j) b = mid + 1;
+    else if (c > j) e = mid;
+    else return mid;
+  }
+  return -1;
+}
+
+__global__ void k_fs_init(int nnz, const int* __restrict__ rowidx, const int* __restrict__ ci,
+                          const double* __restrict__ v, const double* __restrict__ alpha, int m,
+                          double* __restrict__ ainv) {
+  const double a0 = alpha[0];
+  const double a1 = m > 1 ? alpha[1] : 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    double acc = (ci[k] == rowidx[k]) ? a0 : 0.0;
+    if (m > 1) acc = fma(a1, v[k], acc);
+    ainv[k] = acc;
+  }
+}
+
+__global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
+                           const int* __restrict__ ci, const double* __restrict__ v, const double* __restrict__ prev,
+                           double* __restrict__ cur, double* __restrict__ ainv, const double* __restrict__ alpha_p) {
+  const double ap = *alpha_p;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int i = rowidx[k], j = ci[k];
+    double acc = 0.0;
+    for (int q = rp[i]; q < rp[i + 1]; ++q) {
+      const int l = ci[q];
+      const int t = find_col(ci, rp[l], rp[l + 1], j);
+      if (t >= 0) acc = fma(prev[q], v[t], acc);
+    }
+    cur[k] = acc;
+    ainv[k] = fma(ap, acc, ainv[k]);
+  }
+}
+
+int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out, Arena& own, Arena& tmp,
+                           cudaStream_t s) {
+  const int n = A.nrows, nnz = A.nnz;
+  AIRG_TRY(own.csr(out, n, n, nnz));
+  CU_TRY(cudaMemcpyAsync(out.rp, A.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(out.ci, A.ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+  if (nnz == 0) return AIRG_OK;
+  int* rowidx;
+  AIRG_TRY(tmp.alloc(&rowidx, nnz));
+  airg::note_launch(), k_row_index<<<GRID(n)>>>(n, A.rp, rowidx);
+  airg::note_launch(), k_fs_init<<<GRID(nnz)>>>(nnz, rowidx, A.ci, A.v, alpha, m, out.v);
+  KERNEL_CHECK();
+  if (m > 2) {
+    double *pa, *pb;
+    AIRG_TRY(tmp.alloc(&pa, nnz));
+    AIRG_TRY(tmp.alloc(&pb, nnz));
+    const double* prev = A.v;
+    double* cur = pa;
+    for (int p = 2; p < m; ++p) {
+      airg::note_launch(), k_fs_power<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, A.v, prev, cur, out.v, alpha + p);
+      KERNEL_CHECK();
+      prev = cur;
+      cur = (cur == pa) ? pb : pa;
+    }
+  }
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic row-wise SpGEMM with the relative row-wise inf-norm drop (steps 9 and 11).
+// Row i: candidate columns = union of B's rows named by A's row i (bitonic sort + unique in
+// shared memory); each output c_ij = sum over A's row in ascending order of fma(a_il, b_lj, .)
+// (b_lj by binary search); scale; drop |c| < tol * max_j |c_ij| unless (keep_diag and j == i).
+// Rows whose candidate count fits kWarpCap are done by one warp, longer rows by one CTA.
+// ------------------------------------------------------------------------------------------
+constexpr int kWarpCap = 1024;
+constexpr int kSpgWarps = 8;
+constexpr int kBlockCapMax = 32768;
+
+__global__ void k_spgemm_ub(int ar, const int* __restrict__ arp, const int* __restrict__ aci,
+                            const int* __restrict__ brp, long long* __restrict__ ub) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ar; i += (long long)gridDim.x * blockDim.x) {
+    long long t = 0;
+    for (int k = arp[i]; k < arp[i + 1]; ++k) {
+      const int l = aci[k];
+      t += brp[l + 1] - brp[l];
+    }
+    ub[i] = t;
+  }
+}
+
+struct SpgArgs {
+  int ar;
+  const int *arp, *aci;
+  const double* av;
+  const int *brp, *bci;
+  const double* bv;
+  double scale, tol;
+  int keep_diag;
+  const long long* ubo;
+  int* tcol;
+  double* tval;
+  int* cnt;
+  int* long_rows;
+  int* n_long;
+};
+
+// Group-generic pieces (G threads cooperate; sync() is __syncwarp or __syncthreads).
+template <int G>
+struct Grp {
+  __device__ static void sync() {
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+  }
+};
+
+template <int G>
+__device__ void bitonic_sort(int* a, int P, int t) {
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int idx = t; idx < P; idx += G) {
+        const int ixj = idx ^ j;
+        if (ixj > idx) {
+          const int x = a[idx], y = a[ixj];
+          const bool up = ((idx & k) == 0);
+          if ((x > y) == up) { a[idx] = y; a[ixj] = x; }
+        }
+      }
+      Grp<G>::sync();
+    }
+}
+
+// Removes duplicates from the sorted a[0..P) (padding 0x7fffffff at the end) in place, keeping
+// order; returns the number of distinct values.  Chunks of 32 are read completely before any
+// write, and the last original value of the previous chunk is carried in a register.
+__device__ int warp_unique_sorted(int* a, int P, int lane) {
+  int outc = 0, prev_last = -1;
+  for (int base = 0; base < P; base += 32) {
+    const int idx = base + lane;
+    const int val = idx < P ? a[idx] : 0x7fffffff;
+    int prv = __shfl_up_sync(0xffffffffu, val, 1);
+    if (lane == 0) prv = prev_last;
+    const bool kf = val != 0x7fffffff && val != prv;
+    const unsigned bal = __ballot_sync(0xffffffffu, kf);
+    prev_last = __shfl_sync(0xffffffffu, val, 31);
+    __syncwarp();
+    if (kf) a[outc + __popc(bal & ((1u << lane) - 1u))] = val;
+    outc += __popc(bal);
+    __syncwarp();
+  }
+  return outc;
+}
+
+__device__ __forceinline__ double spg_value(const SpgArgs& g, int ab, int ae, int j) {
+  double acc = 0.0;
+  for (int k = ab; k < ae; ++k) {
+    const int l = g.aci[k];
+    const int t = find_col(g.bci, g.brp[l], g.brp[l + 1], j);
+    if (t >= 0) acc = fma(g.av[k], g.bv[t], acc);
+  }
+  return g.scale * acc;
+}
+
+__global__ void __launch_bounds__(kSpgWarps * 32) k_spgemm_warp(SpgArgs g) {
+  __shared__ int sbuf[kSpgWarps][kWarpCap];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* buf = sbuf[wid];
+  const long long gw = (long long)blockIdx.x * kSpgWarps + wid;
+  const long long nw = (long long)gridDim.x * kSpgWarps;
+  for (long long ii = gw; ii < g.ar; ii += nw) {
+    const int i = (int)ii;
+    const long long ub = g.ubo[i + 1] - g.ubo[i];
+    if (ub == 0) { if (lane == 0) g.cnt[i] = 0; continue; }
+    if (ub > kWarpCap) {
+      if (lane == 0) { g.long_rows[atomicAdd(g.n_long, 1)] = i; g.cnt[i] = 0; }
+      continue;
+    }
+    const int ab = g.arp[i], ae = g.arp[i + 1];
+    int off = 0;
+    for (int k = ab; k < ae; ++k) {
+      const int l = g.aci[k];
+      const int b0 = g.brp[l], len = g.brp[l + 1] - b0;
+      for (int t = lane; t < len; t += 32) buf[off + t] = g.bci[b0 + t];
+      off += len;
+    }
+    int P = 32;
+    while (P < ub) P <<= 1;
+    for (int t = (int)ub + lane; t < P; t += 32) buf[t] = 0x7fffffff;
+    __syncwarp();
+    bitonic_sort<32>(buf, P, lane);
+    const int u = warp_unique_sorted(buf, P, lane);
+    // values
+    const long long o = g.ubo[i];
+    double mx = 0.0;
+    for (int t = lane; t < u; t += 32) {
+      const int j = buf[t];
+      const double c = spg_value(g, ab, ae, j);
+      g.tcol[o + t] = j;
+      g.tval[o + t] = c;
+      mx = fmax(mx, fabs(c));
+    }
+    for (int s2 = 16; s2 > 0; s2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
+    const double thr = g.tol * mx;
+    __syncwarp();
+    // drop + compaction in the row's temporary slot
+    int outc = 0;
+    for (int base = 0; base < u; base += 32) {
+      const int t = base + lane;
+      int j = 0;
+      double c = 0.0;
+      bool keep = false;
+      if (t < u) {
+        j = g.tcol[o + t];
+        c = g.tval[o + t];
+        keep = !(fabs(c) < thr) || (g.keep_diag && j == i);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) {
+        const int d = outc + __popc(bal & ((1u << lane) - 1u));
+        g.tcol[o + d] = j;
+        g.tval[o + d] = c;
+      }
+      outc += __popc(bal);
+      __syncwarp();
+    }
+    if (lane == 0) g.cnt[i] = outc;
+  }
+}
+
+// Long rows: one 256-thread CTA per row, dynamic shared memory of P ints.
+__global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __restrict__ rows, int cap) {
+  extern __shared__ int bbuf[];
+  __shared__ int wcnt[8];
+  __shared__ double wmx[8];
+  const int i = rows[blockIdx.x];
+  const int t0 = threadIdx.x, lane = t0 & 31, wid = t0 >> 5;
+  const long long ub = g.ubo[i + 1] - g.ubo[i];
+  const int ab = g.arp[i], ae = g.arp[i + 1];
+  int off = 0;
+  for (int k = ab; k < ae; ++k) {
+    const int l = g.aci[k];
+    const int b0 = g.brp[l], len = g.brp[l + 1] - b0;
+    for (int t = t0; t < len; t += 256) bbuf[off + t] = g.bci[b0 + t];
+    off += len;
+  }
+  int P = 256;
+  while (P < ub) P <<= 1;
+  for (int t = (int)ub + t0; t < P; t += 256) bbuf[t] = 0x7fffffff;
+  __syncthreads();
+  bitonic_sort<256>(bbuf, P, t0);
+  // unique via block-wide chunked compaction (chunk fully read before it is written)
+  __shared__ int prev_last;
+  if (t0 == 0) prev_last = -1;
+  __syncthreads();
+  int u = 0;
+  for (int base = 0; base < P; base += 256) {
+    const int idx = base + t0;
+    const int val = bbuf[idx];
+    const int prv = (t0 == 0) ? prev_last : bbuf[idx - 1];
+    const bool kf = val != 0x7fffffff && val != prv;
+    const unsigned bal = __ballot_sync(0xffffffffu, kf);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, chunk = 0;
+    for (int q = 0; q < 8; ++q) { if (q < wid) before += wcnt[q]; chunk += wcnt[q]; }
+    if (kf) bbuf[u + before + __popc(bal & ((1u << lane) - 1u))] = val;
+    u += chunk;
+    if (t0 == 255) prev_last = val;
+    __syncthreads();
+  }
+  const long long o = g.ubo[i];
+  double mx = 0.0;
+  for (int t = t0; t < u; t += 256) {
+    const int j = bbuf[t];
+    const double c = spg_value(g, ab, ae, j);
+    g.tcol[o + t] = j;
+    g.tval[o + t] = c;
+    mx = fmax(mx, fabs(c));
+  }
+  for (int s2 = 16; s2 > 0; s2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
+  if (lane == 0) wmx[wid] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int q = 0; q < 8; ++q) mx = fmax(mx, wmx[q]);
+  const double thr = g.tol * mx;
+  int outc = 0;
+  for (int base = 0; base < u; base += 256) {
+    const int t = base + t0;
+    int j = 0;
+    double c = 0.0;
+    bool keep = false;
+    if (t < u) {
+      j = g.tcol[o + t];
+      c = g.tval[o + t];
+      keep = !(fabs(c) < thr) || (g.keep_diag && j == i);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0, chunk = 0;
+    for (int q = 0; q < 8; ++q) { if (q < wid) before += wcnt[q]; chunk += wcnt[q]; }
+    if (keep) {
+      const int d = outc + before + __popc(bal & ((1u << lane) - 1u));
+      g.tcol[o + d] = j;
+      g.tval[o + d] = c;
+    }
+    outc += chunk;
+    __syncthreads();
+  }
+  if (t0 == 0) g.cnt[i] = outc;
+  (void)cap;
+}
+
+__global__ void k_spgemm_copy(int ar, const long long* __restrict__ ubo, const int* __restrict__ tcol,
+                              const double* __restrict__ tval, const int* __restrict__ rp, int* __restrict__ ci,
+                              double* __restrict__ v) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = gw; i < ar; i += nw) {
+    const long long o = ubo[i];
+    const int b = rp[i], len = rp[i + 1] - b;
+    for (int t = lane; t < len; t += 32) {
+      ci[b + t] = tcol[o + t];
+      v[b + t] = tval[o + t];
+    }
+  }
+}
+
+int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_diag, DCsr& out, Arena& own,
+           Arena& tmp, cudaStream_t s) {
+  const int ar = A.nrows;
+  long long *ub, *ubo;
+  AIRG_TRY(tmp.alloc(&ub, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&ubo, (size_t)ar + 1));
+  if (ar > 0) airg::note_launch(), k_spgemm_ub<<<GRID(ar)>>>(ar, A.rp, A.ci, B.rp, ub);
+  KERNEL_CHECK();
+  long long total = 0;
+  AIRG_TRY(scan_i64(ub, ubo, ar, tmp, s, &total));
+  SpgArgs g{};
+  g.ar = ar;
+  g.arp = A.rp; g.aci = A.ci; g.av = A.v;
+  g.brp = B.rp; g.bci = B.ci; g.bv = B.v;
+  g.scale = scale; g.tol = tol; g.keep_diag = keep_diag ? 1 : 0;
+  g.ubo = ubo;
+  AIRG_TRY(tmp.alloc(&g.tcol, (size_t)std::max(total, 1LL)));
+  AIRG_TRY(tmp.alloc(&g.tval, (size_t)std::max(total, 1LL)));
+  AIRG_TRY(tmp.alloc(&g.cnt, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&g.long_rows, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&g.n_long, 1));
+  CU_TRY(cudaMemsetAsync(g.n_long, 0, sizeof(int), s));
+  if (ar > 0) {
+    airg::note_launch(), k_spgemm_warp<<<grid_for((long long)ar * 32, kSpgWarps * 32, 152 * 64), kSpgWarps * 32, 0, s>>>(g);
+    KERNEL_CHECK();
+    int nlong = 0;
+    CU_TRY(cudaMemcpyAsync(&nlong, g.n_long, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    if (nlong > 0) {
+      // capacity: the longest candidate list among the long rows (host-side max over ub)
+      std::vector<int> lr(nlong);
+      CU_TRY(cudaMemcpyAsync(lr.data(), g.long_rows, sizeof(int) * nlong, cudaMemcpyDeviceToHost, s));
+      std::vector<long long> hub(ar + 1);
+      CU_TRY(cudaMemcpyAsync(hub.data(), ubo, sizeof(long long) * (ar + 1), cudaMemcpyDeviceToHost, s));
+      CU_TRY(cudaStreamSynchronize(s));
+      long long mx = 0;
+      for (int r : lr) mx = std::max(mx, hub[r + 1] - hub[r]);
+      if (mx > kBlockCapMax) return AIRG_ERR_UNSUPPORTED;
+      int P = 256;
+      while (P < mx) P <<= 1;
+      const size_t smem = sizeof(int) * (size_t)P;
+      if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      airg::note_launch(), k_spgemm_block<<<nlong, 256, smem, s>>>(g, g.long_rows, P);
+      KERNEL_CHECK();
+    }
+  }
+  int* rp;
+  AIRG_TRY(own.alloc(&rp, (size_t)ar + 1));
+  long long nnz = 0;
+  AIRG_TRY(scan_i32(g.cnt, rp, ar, tmp, s, &nnz));
+  if (nnz > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
+  out.nrows = ar;
+  out.ncols = B.ncols;
+  out.nnz = (int)nnz;
+  out.rp = rp;
+  AIRG_TRY(own.alloc(&out.ci, (size_t)nnz));
+  AIRG_TRY(own.alloc(&out.v, (size_t)nnz));
+  if (ar > 0) airg::note_launch(), k_spgemm_copy<<<grid_for((long long)ar * 32, 256, 152 * 64), 256, 0, s>>>(ar, ubo, g.tcol, g.tval, rp, out.ci, out.v);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Step 10: one-point prolongation.  Each F-point takes the strong C dependency with the largest
+// |a_ij| (ties: smallest j), else the largest nonzero C entry of its row, weight 1.
+// ------------------------------------------------------------------------------------------
+__global__ void k_one_point(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                            const uint8_t* __restrict__ strong, const int8_t* __restrict__ cf,
+                            const int* __restrict__ fpos, int* __restrict__ w) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    if (cf[i] != kF) continue;
+    int best = -1;
+    double bv = -1.0;
+    for (int pass = 0; pass < 2 && best < 0; ++pass)
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j == i || cf[j] != kC || v[k] == 0.0) continue;
+        if (pass == 0 && !strong[k]) continue;
+        const double a = fabs(v[k]);
+        if (a > bv) { bv = a; best = j; }
+      }
+    w[fpos[i]] = best >= 0 ? best - fpos[best] : -1;
+  }
+}
+
+// P (n x n_c, natural rows): C row -> its C index, F row -> w (if any), values 1.
+__global__ void k_P_count(int n, const int8_t* __restrict__ cf, const int* __restrict__ fpos, const int* __restrict__ w,
+                          int* __restrict__ cnt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    cnt[i] = (cf[i] == kF) ? (w[fpos[i]] >= 0) : 1;
+}
+__global__ void k_P_fill(int n, const int8_t* __restrict__ cf, const int* __restrict__ fpos, const int* __restrict__ w,
+                         const int* __restrict__ rp, int* __restrict__ ci, double* __restrict__ v) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    const int c = (cf[i] == kF) ? w[fpos[i]] : i - fpos[i];
+    if (c >= 0) { ci[rp[i]] = c; v[rp[i]] = 1.0; }
+  }
+}
+// R = [Z I] in natural column numbering: row c = Z row c (columns Fnat[f]) merged with (Cnat[c], 1).
+__global__ void k_R_fill(int nc, const int* __restrict__ zrp, const int* __restrict__ zci, const double* __restrict__ zv,
+                         const int* __restrict__ Fnat, const int* __restrict__ Cnat, int* __restrict__ rrp,
+                         int* __restrict__ rci, double* __restrict__ rv) {
+  for (long long cc = (long long)blockIdx.x * blockDim.x + threadIdx.x; cc < nc; cc += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)cc;
+    const int b = zrp[c], e = zrp[c + 1];
+    int o = b + c;
+    rrp[c] = o;
+    if (c == nc - 1) rrp[nc] = e + nc;
+    const int self = Cnat[c];
+    bool placed = false;
+    for (int k = b; k < e; ++k) {
+      const int j = Fnat[zci[k]];
+      if (!placed && self < j) { rci[o] = self; rv[o++] = 1.0; placed = true; }
+      rci[o] = j;
+      rv[o++] = zv[k];
+    }
+    if (!placed) { rci[o] = self; rv[o] = 1.0; }
+  }
+}
+
+int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coarsest, LevelBuild& L,
+                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  L.A = A;
+  L.n = n;
+  const int m = p.poly_order + 1, mc = p.coarse_poly_order + 1;
+  bool coarsest = force_coarsest || n <= p.coarse_size || n < m;
+  uint8_t* strong = nullptr;
+  if (!coarsest) {
+    AIRG_TRY(own.alloc(&L.cf, n));
+    AIRG_TRY(tmp.alloc(&strong, std::max(A.nnz, 1)));
+    int nf = 0;
+    AIRG_TRY(cf_split(A, p, level, L.cf, strong, &nf, tmp, s));
+    if (nf == 0 || nf == n) coarsest = true;
+    L.nf = nf;
+    L.nc = n - nf;
+  }
+  if (coarsest) {
+    L.coarsest = true;
+    L.nf = 0;
+    L.nc = 0;
+    L.m = mc;
+    AIRG_TRY(own.alloc(&L.alpha, mc));
+    AIRG_TRY(poly_fit(A, mc, p.seed, level, L.alpha, &L.fitted, tmp, s));
+    AIRG_TRY(fixed_sparsity_inverse(A, L.alpha, mc, L.Ainv, own, tmp, s));
+    Ac_out = DCsr{};
+    return AIRG_OK;
+  }
+  const int nf = L.nf, nc = L.nc;
+  int *isF, *fpos;
+  AIRG_TRY(tmp.alloc(&isF, n));
+  AIRG_TRY(tmp.alloc(&fpos, (size_t)n + 1));
+  airg::note_launch(), k_isF<<<GRID(n)>>>(n, L.cf, isF);
+  AIRG_TRY(scan_i32(isF, fpos, n, tmp, s, nullptr));
+  AIRG_TRY(own.alloc(&L.pos, n));
+  AIRG_TRY(own.alloc(&L.Fnat, nf));
+  AIRG_TRY(own.alloc(&L.Cnat, nc));
+  airg::note_launch(), k_cf_maps<<<GRID(n)>>>(n, nf, L.cf, fpos, L.pos, L.Fnat, L.Cnat);
+  int *cFF, *cFC, *cCF;
+  AIRG_TRY(tmp.alloc(&cFF, nf));
+  AIRG_TRY(tmp.alloc(&cFC, nf));
+  AIRG_TRY(tmp.alloc(&cCF, nc));
+  airg::note_launch(), k_extract_count<<<GRID(n)>>>(n, A.rp, A.ci, L.cf, fpos, cFF, cFC, cCF);
+  KERNEL_CHECK();
+  long long zff, zfc, zcf;
+  L.Aff.nrows = nf; L.Aff.ncols = nf;
+  L.Afc.nrows = nf; L.Afc.ncols = nc;
+  L.Acf.nrows = nc; L.Acf.ncols = nf;
+  AIRG_TRY(own.alloc(&L.Aff.rp, (size_t)nf + 1));
+  AIRG_TRY(own.alloc(&L.Afc.rp, (size_t)nf + 1));
+  AIRG_TRY(own.alloc(&L.Acf.rp, (size_t)nc + 1));
+  AIRG_TRY(scan_i32(cFF, L.Aff.rp, nf, tmp, s, &zff));
+  AIRG_TRY(scan_i32(cFC, L.Afc.rp, nf, tmp, s, &zfc));
+  AIRG_TRY(scan_i32(cCF, L.Acf.rp, nc, tmp, s, &zcf));
+  L.Aff.nnz = (int)zff; L.Afc.nnz = (int)zfc; L.Acf.nnz = (int)zcf;
+  AIRG_TRY(own.alloc(&L.Aff.ci, zff)); AIRG_TRY(own.alloc(&L.Aff.v, zff));
+  AIRG_TRY(own.alloc(&L.Afc.ci, zfc)); AIRG_TRY(own.alloc(&L.Afc.v, zfc));
+  AIRG_TRY(own.alloc(&L.Acf.ci, zcf)); AIRG_TRY(own.alloc(&L.Acf.v, zcf));
+  airg::note_launch(), k_extract_fill<<<GRID(n)>>>(n, A.rp, A.ci, A.v, L.cf, fpos, L.Aff, L.Afc, L.Acf);
+  KERNEL_CHECK();
+  // steps 3-8
+  L.m = m;
+  AIRG_TRY(own.alloc(&L.alpha, m));
+  AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, &L.fitted, tmp, s));
+  AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s));
+  // step 9
+  AIRG_TRY(spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false, L.Z, own, tmp, s));
+  // step 10
+  AIRG_TRY(own.alloc(&L.w, nf));
+  airg::note_launch(), k_one_point<<<GRID(n)>>>(n, A.rp, A.ci, A.v, strong, L.cf, fpos, L.w);
+  KERNEL_CHECK();
+  // step 11: A_c = R (A P)
+  DCsr P;
+  P.nrows = n; P.ncols = nc;
+  int* pc;
+  AIRG_TRY(tmp.alloc(&pc, n));
+  AIRG_TRY(tmp.alloc(&P.rp, (size_t)n + 1));
+  airg::note_launch(), k_P_count<<<GRID(n)>>>(n, L.cf, fpos, L.w, pc);
+  long long pz = 0;
+  AIRG_TRY(scan_i32(pc, P.rp, n, tmp, s, &pz));
+  P.nnz = (int)pz;
+  AIRG_TRY(tmp.alloc(&P.ci, pz));
+  AIRG_TRY(tmp.alloc(&P.v, pz));
+  airg::note_launch(), k_P_fill<<<GRID(n)>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
+  KERNEL_CHECK();
+  DCsr AP;
+  AIRG_TRY(spgemm(A, P, 1.0, 0.0, false, AP, tmp, tmp, s));
+  DCsr R;
+  R.nrows = nc; R.ncols = n; R.nnz = L.Z.nnz + nc;
+  AIRG_TRY(tmp.alloc(&R.rp, (size_t)nc + 1));
+  AIRG_TRY(tmp.alloc(&R.ci, R.nnz));
+  AIRG_TRY(tmp.alloc(&R.v, R.nnz));
+  if (nc > 0) airg::note_launch(), k_R_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, L.Fnat, L.Cnat, R.rp, R.ci, R.v);
+  KERNEL_CHECK();
+  AIRG_TRY(spgemm(R, AP, 1.0, p.drop_Ac, true, Ac_out, own, tmp, s));
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Solve-phase operators in the F-then-C numbering
+// ------------------------------------------------------------------------------------------
+__global__ void k_af_fill(int nf, DCsr Aff, DCsr Afc, const int* __restrict__ pos_next, DCsr AF) {
+  for (long long ff = (long long)blockIdx.x * blockDim.x + threadIdx.x; ff < nf; ff += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)ff;
+    int o = Aff.rp[f] + Afc.rp[f];
+    AF.rp[f] = o;
+    if (f == nf - 1) AF.rp[nf] = Aff.rp[nf] + Afc.rp[nf];
+    for (int k = Aff.rp[f]; k < Aff.rp[f + 1]; ++k) { AF.ci[o] = Aff.ci[k]; AF.v[o++] = Aff.v[k]; }
+    for (int k = Afc.rp[f]; k < Afc.rp[f + 1]; ++k) {
+      const int c = Afc.ci[k];
+      AF.ci[o] = nf + (pos_next ? pos_next[c] : c);
+      AF.v[o++] = Afc.v[k];
+    }
+  }
+}
+__global__ void k_perm_rows_count(int n, const int* __restrict__ rp, const int* __restrict__ pos, int* __restrict__ cnt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    cnt[pos ? pos[i] : i] = rp[i + 1] - rp[i];
+}
+// row pos[i] of out <- row i of A; columns mapped by cpos (nullptr: kept) plus coff
+__global__ void k_perm_rows_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                                 const int* __restrict__ pos, const int* __restrict__ cpos, const int* __restrict__ orp,
+                                 int* __restrict__ oci, double* __restrict__ ov) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int o = orp[pos ? pos[i] : i];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      oci[o] = cpos ? cpos[j] : j;
+      ov[o++] = v[k];
+    }
+  }
+}
+__global__ void k_w_solve(int nf, const int* __restrict__ w, const int* __restrict__ pos_next, int* __restrict__ ws) {
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    const int c = w[f];
+    ws[f] = c < 0 ? -1 : (pos_next ? pos_next[c] : c);
+  }
+}
+
+// Nested solve numbering of a level: F-points first (ascending), then the C-points in the next
+// level's own nested numbering.  lay(i) = pos(i) for F, n_f + lay_next(pos(i) - n_f) for C.
+__global__ void k_compose_layout(int n, int nf, const int* __restrict__ pos, const int* __restrict__ lay_next,
+                                 int* __restrict__ lay) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int p = pos[i];
+    lay[i] = (p < nf || !lay_next) ? p : nf + lay_next[p - nf];
+  }
+}
+
+int compose_layout(const LevelBuild& L, const int* lay_next, int* lay, cudaStream_t s) {
+  if (L.n > 0) airg::note_launch(), k_compose_layout<<<GRID(L.n)>>>(L.n, L.nf, L.pos, lay_next, lay);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, Arena& own,
+                    Arena& tmp, cudaStream_t s) {
+  const int nf = L.nf, nc = L.nc;
+  AIRG_TRY(own.csr(AF, nf, nf + nc, L.Aff.nnz + L.Afc.nnz));
+  if (nf > 0) airg::note_launch(), k_af_fill<<<GRID(nf)>>>(nf, L.Aff, L.Afc, pos_next, AF);
+  KERNEL_CHECK();
+  AIRG_TRY(own.csr(Zs, nc, nf, L.Z.nnz));
+  int* cnt;
+  AIRG_TRY(tmp.alloc(&cnt, std::max(nc, 1)));
+  if (nc > 0) airg::note_launch(), k_perm_rows_count<<<GRID(nc)>>>(nc, L.Z.rp, pos_next, cnt);
+  AIRG_TRY(scan_i32(cnt, Zs.rp, nc, tmp, s, nullptr));
+  if (nc > 0) airg::note_launch(), k_perm_rows_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, pos_next, nullptr, Zs.rp, Zs.ci, Zs.v);
+  AIRG_TRY(own.alloc(ws, std::max(nf, 1)));
+  if (nf > 0) airg::note_launch(), k_w_solve<<<GRID(nf)>>>(nf, L.w, pos_next, *ws);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+int permute_matrix(const DCsr& A, const int* pos, DCsr& out, Arena& own, Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  AIRG_TRY(own.csr(out, n, n, A.nnz));
+  int* cnt;
+  AIRG_TRY(tmp.alloc(&cnt, std::max(n, 1)));
+  if (n > 0) airg::note_launch(), k_perm_rows_count<<<GRID(n)>>>(n, A.rp, pos, cnt);
+  AIRG_TRY(scan_i32(cnt, out.rp, n, tmp, s, nullptr));
+  if (n > 0) airg::note_launch(), k_perm_rows_fill<<<GRID(n)>>>(n, A.rp, A.ci, A.v, pos, pos, out.rp, out.ci, out.v);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+}  // namespace airg

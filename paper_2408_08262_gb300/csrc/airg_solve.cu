@@ -1,0 +1,312 @@
+// Solve phase: the AIRG V-cycle (Section "Results": restriction with R = [Z I], recursion,
+// one-point prolongation, up F-point smoothing only; coarsest level: iterations of the assembled
+// GMRES polynomial) and the outer iterations (right-preconditioned FGMRES with CGS2, or the
+// paper's undamped Richardson).  All vectors are kept in the level-0 F-then-C numbering; the
+// permutation is applied once on entry and once on exit.
+#include <cmath>
+#include <cstring>
+
+#include "airg_hier.cuh"
+
+namespace airg {
+
+// ------------------------------------------------------------------------------------------
+// Kernel timing (only when profiling is enabled)
+// ------------------------------------------------------------------------------------------
+static cudaEvent_t prof_event(Profiler& P) {
+  if (P.used == P.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    P.pool.push_back(e);
+  }
+  return P.pool[P.used++];
+}
+struct ProfScope {
+  Profiler& P;
+  cudaStream_t s;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(Profiler& P_, cudaStream_t s_, int c, double b) : P(P_), s(s_), cls(c), bytes(b) {
+    if (P.on && ((P.mask >> cls) & 1u)) {
+      a = prof_event(P);
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(P);
+      if (b) {
+        cudaEventRecord(b, s);
+        P.pending.push_back({cls, a, b, bytes});
+      }
+    }
+  }
+};
+
+int prof_flush(airg_hierarchy* H) {
+  Profiler& P = H->prof;
+  if (P.pending.empty()) return AIRG_OK;
+  CU_TRY(cudaStreamSynchronize(H->s));
+  for (auto& r : P.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      P.launches[r.cls] += 1;
+      P.ms[r.cls] += ms;
+      P.bytes[r.cls] += r.bytes;
+    }
+  }
+  P.pending.clear();
+  P.used = 0;
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Workspaces
+// ------------------------------------------------------------------------------------------
+int solve_alloc(airg_hierarchy* H, int restart) {
+  if (H->restart_alloc >= restart && H->V) return AIRG_OK;
+  Arena& a = H->solve_mem;
+  const size_t n = (size_t)std::max(H->n0, 1);
+  AIRG_TRY(a.alloc(&H->V, n * (restart + 1)));
+  AIRG_TRY(a.alloc(&H->Zk, n * restart));
+  if (!H->w) {
+    AIRG_TRY(a.alloc(&H->w, n));
+    AIRG_TRY(a.alloc(&H->r, n));
+    AIRG_TRY(a.alloc(&H->bwork, n));
+    AIRG_TRY(a.alloc(&H->rtmp, n));
+    AIRG_TRY(a.alloc(&H->bp, n));
+    AIRG_TRY(a.alloc(&H->xp, n));
+    AIRG_TRY(a.alloc(&H->dsc, 256));
+    AIRG_TRY(reducer_init(H->red, a, H->s));
+    if (!H->hsc) CU_TRY(cudaMallocHost((void**)&H->hsc, 256 * sizeof(double)));
+  }
+  H->restart_alloc = restart;
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// V-cycle.  b0: level-0 rhs (solve numbering, not modified); x0: output (n0 entries).  Level l's
+// rhs lives in bwork[off_l, off_l + n_l) for l >= 1; level l's solution in x0[off_l, ...).
+// ------------------------------------------------------------------------------------------
+int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
+  cudaStream_t s = H->s;
+  Profiler& P = H->prof;
+  const int L = (int)H->lv.size() - 1;
+  auto bptr = [&](int l) -> const double* { return l == 0 ? b0 : H->bwork + H->lv[l].off; };
+  // restriction down the hierarchy: b_{l+1} = b_C + Z b_F
+  for (int l = 0; l < L; ++l) {
+    const SolveLevel& S = H->lv[l];
+    const double* bl = bptr(l);
+    double* bn = H->bwork + H->lv[l + 1].off;
+    ProfScope ps(P, s, PC_RESTRICT, S.bytes_Z);
+    AIRG_TRY(dev_spmv(S.Z, bl, bl + S.nf, bn, SPMV_ADDB, S.lanes_Z, s));
+  }
+  // coarsest level: x = Ainv b, then x += Ainv (b - A x)
+  {
+    const SolveLevel& S = H->lv[L];
+    const double* bl = bptr(L);
+    double* xl = x0 + S.off;
+    {
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv);
+      AIRG_TRY(dev_spmv(S.Ainv, bl, nullptr, xl, SPMV_SET, S.lanes_Ainv, s));
+    }
+    for (int it = 1; it < H->p.coarse_iters; ++it) {
+      {
+        ProfScope ps(P, s, PC_COARSEST, S.bytes_A);
+        AIRG_TRY(dev_spmv(S.A, xl, bl, H->rtmp, SPMV_RESID, S.lanes_A, s));
+      }
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv);
+      AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
+    }
+  }
+  // prolongation and up F-point smoothing
+  for (int l = L - 1; l >= 0; --l) {
+    const SolveLevel& S = H->lv[l];
+    const double* bl = bptr(l);
+    double* xl = x0 + S.off;
+    {
+      ProfScope ps(P, s, PC_PROLONG, (double)S.nf * 16.0);
+      dev_gather_prolong(xl, S.nf, S.w, s);
+    }
+    for (int sm = 0; sm < H->p.n_smooth_up; ++sm) {
+      {
+        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF);
+        AIRG_TRY(dev_spmv(S.AF, xl, bl, H->rtmp, SPMV_RESID, S.lanes_AF, s));
+      }
+      ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv);
+      AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
+    }
+  }
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Outer iterations
+// ------------------------------------------------------------------------------------------
+static int read_scalars(airg_hierarchy* H, int count) {
+  CU_TRY(cudaMemcpyAsync(H->hsc, H->dsc, sizeof(double) * count, cudaMemcpyDeviceToHost, H->s));
+  CU_TRY(cudaStreamSynchronize(H->s));
+  return AIRG_OK;
+}
+
+enum { DS_H1 = 0, DS_H2 = 64, DS_NRM = 128, DS_AUX = 129, DS_Y = 160 };
+
+// true residual r = bp - A xp and its squared norm into hsc[DS_NRM]
+static int true_residual(airg_hierarchy* H) {
+  const int n = H->n0;
+  {
+    ProfScope ps(H->prof, H->s, PC_TOP_OP, H->bytes_A0);
+    AIRG_TRY(dev_spmv(H->A0s, H->xp, H->bp, H->r, SPMV_RESID, H->lanes_A0, H->s));
+  }
+  AIRG_TRY(dev_nrm2sq(H->r, n, H->dsc + DS_NRM, H->red, H->s));
+  return read_scalars(H, DS_NRM + 1);
+}
+
+static void to_solve_order(airg_hierarchy* H, const double* in, double* out) {
+  if (H->pos0) dev_permute(in, H->pos0, out, H->n0, false, H->s);
+  else cudaMemcpyAsync(out, in, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s);
+}
+static void from_solve_order(airg_hierarchy* H, const double* in, double* out) {
+  if (H->pos0) dev_permute(in, H->pos0, out, H->n0, true, H->s);
+  else cudaMemcpyAsync(out, in, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s);
+}
+
+static int start(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, double* bnorm) {
+  const int n = H->n0;
+  to_solve_order(H, b, H->bp);
+  if (o->x0_zero) CU_TRY(cudaMemsetAsync(H->xp, 0, sizeof(double) * n, H->s));
+  else to_solve_order(H, x, H->xp);
+  AIRG_TRY(dev_nrm2sq(H->bp, n, H->dsc + DS_AUX, H->red, H->s));
+  AIRG_TRY(read_scalars(H, DS_AUX + 1));
+  *bnorm = std::sqrt(H->hsc[DS_AUX]);
+  return AIRG_OK;
+}
+
+int solve_fgmres(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info) {
+  const int n = H->n0, restart = o->restart;
+  cudaStream_t s = H->s;
+  AIRG_TRY(solve_alloc(H, restart));
+  double bn = 0.0;
+  AIRG_TRY(start(H, b, x, o, &bn));
+  int iters = 0;
+  double relres = 0.0;
+  int status = AIRG_OK;
+  if (bn == 0.0) {
+    CU_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    info->iters = 0;
+    info->relres = 0.0;
+    info->status = AIRG_OK;
+    return AIRG_OK;
+  }
+  AIRG_TRY(true_residual(H));
+  double beta = std::sqrt(H->hsc[DS_NRM]);
+  relres = beta / bn;
+  std::vector<double> Hh((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
+  while (true) {
+    if (!(relres == relres) || std::isinf(relres)) { status = AIRG_ERR_NAN; break; }
+    if (relres <= o->rtol) break;
+    if (iters >= o->max_it) { status = AIRG_NOT_CONVERGED; break; }
+    dev_scale(H->r, beta, H->V, n, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < restart && iters < o->max_it; ++j) {
+      double* vj = H->V + (size_t)j * n;
+      double* zj = H->Zk + (size_t)j * n;
+      AIRG_TRY(vcycle_solve_order(H, vj, zj));
+      {
+        ProfScope ps(H->prof, s, PC_TOP_OP, H->bytes_A0);
+        AIRG_TRY(dev_spmv(H->A0s, zj, nullptr, H->w, SPMV_SET, H->lanes_A0, s));
+      }
+      {
+        ProfScope ps(H->prof, s, PC_GS, 8.0 * n * (3.0 * (j + 1) + 5.0));
+        AIRG_TRY(dev_gs_pass(H->V, n, j + 1, H->w, n, nullptr, H->dsc + DS_H1, nullptr, H->red, s));
+        AIRG_TRY(dev_gs_pass(H->V, n, j + 1, H->w, n, H->dsc + DS_H1, H->dsc + DS_H2, nullptr, H->red, s));
+        AIRG_TRY(dev_gs_pass(H->V, n, j + 1, H->w, n, H->dsc + DS_H2, nullptr, H->dsc + DS_NRM, H->red, s));
+      }
+      AIRG_TRY(read_scalars(H, DS_NRM + 1));
+      double* h = &Hh[(size_t)j * (restart + 1)];
+      for (int i = 0; i <= j; ++i) h[i] = H->hsc[DS_H1 + i] + H->hsc[DS_H2 + i];
+      const double hj1 = std::sqrt(H->hsc[DS_NRM]);
+      h[j + 1] = hj1;
+      for (int i = 0; i < j; ++i) {
+        const double t1 = h[i], t2 = h[i + 1];
+        h[i] = cs[i] * t1 + sn[i] * t2;
+        h[i + 1] = -sn[i] * t1 + cs[i] * t2;
+      }
+      const double d = std::hypot(h[j], h[j + 1]);
+      double c_ = 1.0, s_ = 0.0;
+      if (d != 0.0) { c_ = h[j] / d; s_ = h[j + 1] / d; }
+      h[j] = c_ * h[j] + s_ * h[j + 1];
+      h[j + 1] = 0.0;
+      cs[j] = c_;
+      sn[j] = s_;
+      g[j + 1] = -s_ * g[j];
+      g[j] = c_ * g[j];
+      iters++;
+      const double est = std::fabs(g[j + 1]) / bn;
+      if (est <= o->rtol || hj1 == 0.0 || !(est == est)) { ++j; break; }
+      dev_scale(H->w, hj1, H->V + (size_t)(j + 1) * n, n, s);
+    }
+    const int k = j;
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < k; ++q) t -= Hh[(size_t)q * (restart + 1) + i] * y[q];
+      y[i] = t / Hh[(size_t)i * (restart + 1) + i];
+    }
+    CU_TRY(cudaMemcpyAsync(H->dsc + DS_Y, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    AIRG_TRY(dev_multi_axpy(H->Zk, n, k, H->dsc + DS_Y, H->xp, n, s));
+    AIRG_TRY(true_residual(H));
+    beta = std::sqrt(H->hsc[DS_NRM]);
+    relres = beta / bn;
+  }
+  from_solve_order(H, H->xp, x);
+  KERNEL_CHECK();
+  CU_TRY(cudaStreamSynchronize(s));
+  AIRG_TRY(prof_flush(H));
+  info->iters = iters;
+  info->relres = relres;
+  info->status = status;
+  return status;
+}
+
+int solve_richardson(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info) {
+  const int n = H->n0;
+  cudaStream_t s = H->s;
+  AIRG_TRY(solve_alloc(H, 1));
+  double bn = 0.0;
+  AIRG_TRY(start(H, b, x, o, &bn));
+  int iters = 0, status = AIRG_OK;
+  double relres = 0.0;
+  if (bn == 0.0) {
+    CU_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    info->iters = 0;
+    info->relres = 0.0;
+    info->status = AIRG_OK;
+    return AIRG_OK;
+  }
+  const double one = 1.0;
+  CU_TRY(cudaMemcpyAsync(H->dsc + DS_Y, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  while (true) {
+    AIRG_TRY(true_residual(H));
+    relres = std::sqrt(H->hsc[DS_NRM]) / bn;
+    if (!(relres == relres) || std::isinf(relres)) { status = AIRG_ERR_NAN; break; }
+    if (relres <= o->rtol) break;
+    if (iters >= o->max_it) { status = AIRG_NOT_CONVERGED; break; }
+    AIRG_TRY(vcycle_solve_order(H, H->r, H->Zk));
+    AIRG_TRY(dev_multi_axpy(H->Zk, n, 1, H->dsc + DS_Y, H->xp, n, s));
+    iters++;
+  }
+  from_solve_order(H, H->xp, x);
+  KERNEL_CHECK();
+  CU_TRY(cudaStreamSynchronize(s));
+  AIRG_TRY(prof_flush(H));
+  info->iters = iters;
+  info->relres = relres;
+  info->status = status;
+  return status;
+}
+
+}  // namespace airg

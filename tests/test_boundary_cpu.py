@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every entry point include/airg.h declares (no GPU
+calls are made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "airg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(airg_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2408_08262_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("airg_setup", "airg_solve", "airg_free", "airg_cf_split"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(libpath):
+    from paper_2408_08262_gb300 import airg
+    assert sorted(airg.EXPORTED) == declared_functions()
+
+
+def test_params_default_and_status_strings(libpath):
+    from paper_2408_08262_gb300 import airg
+    p = airg._Params()
+    airg.lib().airg_params_default(ctypes.byref(p))
+    assert p.strong_threshold == 0.5 and p.ddc_fraction == 0.1 and p.pmisr_max_loops == 3
+    assert p.drop_R == 0.01 and p.drop_Ac == 0.001 and p.n_smooth_up == 2 and p.coarse_poly_order == 12
+    assert p.seed == 240808262
+    # Python defaults mirror the C defaults
+    d = airg.Params()
+    for k, _ in airg._Params._fields_:
+        assert getattr(p, k) == getattr(d, k), k
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert airg.lib().airg_status_string(code)
+
+
+def test_setup_rejects_null_arguments_without_gpu(libpath):
+    from paper_2408_08262_gb300 import airg
+    out = ctypes.c_void_p()
+    assert airg.lib().airg_setup(None, None, None, ctypes.byref(out)) == -1
+    assert airg.lib().airg_solve(None, None, None, None, None, None) == -1
