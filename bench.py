@@ -285,6 +285,10 @@ def main():
                            "levels": lv0["levels"], "grid_complexity": round(lv0["grid"], 3),
                            "operator_complexity": round(lv0["operator"], 3), "iters": med(iters),
                            "setup_ms": round(med(setup_ms), 2), "solve_ms": round(med(solve_ms), 2),
+                           "setup_phase_ms": {k: round(v, 2) for k, v in lv0["phase_ms"].items()},
+                           "solve_kernels_first_step": {c: {"launches": kt0[c]["launches"], "ms": round(kt0[c]["ms"], 3),
+                                                            "GBps": round(kt0[c]["bytes"] / max(kt0[c]["ms"], 1e-9) / 1e6, 1)}
+                                                        for c in classes},
                            "solve_only_dofs_per_s": p.n / (med(solve_ms) / 1e3),
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},

@@ -63,13 +63,13 @@ typedef struct {
 
 /* Setup parameters.  Defaults (airg_params_default) follow the paper's parallel settings
  * (Section "Parallel results"): strength 0.5, n_loops^max = 3, DDC fraction 10 %, drop 0.01 on Z
- * and 0.001 on the coarse matrices; two up F-smooths (Section "Results"); the coarse solve uses
+ * and 0.001 on the coarse matrices, 6th-order polynomials (m = 7) with first-order fixed sparsity; two up F-smooths (Section "Results"); the coarse solve uses
  * three iterations of a 12th-order fixed-sparsity polynomial (Section "Timing results"). */
 typedef struct {
   double strong_threshold;  /* alpha in eq. soc, in [0, 1] */
   double ddc_fraction;      /* fraction of F-points DDC converts, in [0, 1] */
   int pmisr_max_loops;      /* n_loops^max of Algorithm 1; <= 0 means no cap */
-  int poly_order;           /* degree d of the GMRES polynomial on A_ff (m = d+1 coefficients) */
+  int poly_order;           /* degree d of the GMRES polynomial on A_ff (m = d+1 coefficients), <= 14 */
   int coarse_poly_order;    /* degree of the coarsest-level polynomial */
   int coarse_iters;         /* iterations of the coarsest-level polynomial solve (>= 1) */
   int coarse_size;          /* a level with n <= coarse_size is the coarsest */
@@ -136,9 +136,14 @@ void airg_free(airg_hierarchy* H);
 int airg_num_levels(const airg_hierarchy* H);
 
 /* Per-level sizes into info[0..15] (host): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
- * nnz(Z), coarsest flag, nnz(A_cf), fitted polynomial coefficients, nnz(AF solve operator),
- * reserved (0) x4.  Level -1 gives totals: levels, grid complexity x1e6, operator complexity x1e6,
- * storage complexity x1e6 (eq. mat_store), setup ms x1e3. */
+ * nnz(Z), coarsest flag, nnz(A_cf), fitted polynomial coefficients, nnz(AF solve operator), and the
+ * level's setup time in microseconds split as in the paper's per-component setup figure:
+ * [12] CF splitting + extraction, [13] GMRES polynomial (steps 3-8), [14] restrictor product,
+ * [15] prolongator + coarse matrix.
+ * Level -1 gives totals: [0] levels, [1] grid complexity x1e6, [2] operator complexity x1e6,
+ * [3] storage complexity x1e6 (eq. mat_store), [4] setup wall ms x1e3, [5..9] summed microseconds of
+ * the five phases (CF splitting, extraction, polynomial, restrictor, prolongator + coarse matrix),
+ * [10] microseconds spent building the solve-phase layout. */
 int airg_level_info(const airg_hierarchy* H, int level, int64_t* info);
 
 /* Copies a level operator to HOST arrays (sizes from airg_level_info).
@@ -174,6 +179,9 @@ int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t
  * once).  Every call of airg_profile_enable resets the sums. */
 int airg_profile_enable(airg_hierarchy* H, int enable);
 int airg_kernel_times(airg_hierarchy* H, int64_t* launches, double* ms, double* bytes, int nclasses);
+/* The same sums restricted to the launches that worked on hierarchy level `level` (classes 3 and 6
+ * are counted on level 0). */
+int airg_kernel_times_level(airg_hierarchy* H, int level, int64_t* launches, double* ms, double* bytes, int nclasses);
 
 /* Total number of CUDA kernel launches this library has issued in the process (all hierarchies,
  * all calls).  Used to count the GPU work of a timed region. */

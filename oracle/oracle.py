@@ -50,14 +50,15 @@ def lib():
 @dataclass
 class Params:
     """AIRG parameters; defaults follow the paper's parallel settings (Section "Parallel
-    results"): strength 0.5, 3 PMISR loops, 10 % DDC, drops 0.01 (R) / 0.001 (A_c), 2 up smooths,
+    results"): strength 0.5, 3 PMISR loops, 10 % DDC, drops 0.01 (R) / 0.001 (A_c), 6th-order
+    polynomials with first-order fixed sparsity (Section "GMRES polynomial order"), 2 up smooths,
     coarse solve 3 iterations of a 12th-order polynomial."""
     strong_threshold: float = 0.5
     ddc_fraction: float = 0.1
     drop_R: float = 0.01
     drop_Ac: float = 0.001
     pmisr_max_loops: int = 3
-    poly_order: int = 2
+    poly_order: int = 6
     coarse_poly_order: int = 12
     coarse_iters: int = 3
     coarse_size: int = 64

@@ -70,6 +70,7 @@ def lib():
         L.airg_export_layout.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
         L.airg_profile_enable.argtypes = [C.c_void_p, C.c_int]
         L.airg_kernel_times.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.airg_kernel_times_level.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.airg_status_string.restype = C.c_char_p
         L.airg_launch_count.restype = C.c_int64
         L.airg_params_default.argtypes = [C.POINTER(_Params)]
@@ -80,7 +81,8 @@ def lib():
 
 EXPORTED = ["airg_params_default", "airg_setup", "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
             "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
-            "airg_profile_enable", "airg_kernel_times", "airg_launch_count", "airg_status_string"]
+            "airg_profile_enable", "airg_kernel_times", "airg_kernel_times_level", "airg_launch_count",
+            "airg_status_string"]
 
 
 def launch_count() -> int:
@@ -93,7 +95,7 @@ class Params:
     strong_threshold: float = 0.5
     ddc_fraction: float = 0.1
     pmisr_max_loops: int = 3
-    poly_order: int = 2
+    poly_order: int = 6
     coarse_poly_order: int = 12
     coarse_iters: int = 3
     coarse_size: int = 64
@@ -161,9 +163,11 @@ class Hierarchy:
         _check(lib().airg_level_info(self._h, level, info.ctypes.data), "airg_level_info")
         if level == -1:
             return dict(levels=int(info[0]), grid=info[1] / 1e6, operator=info[2] / 1e6, storage=info[3] / 1e6,
-                        setup_ms=info[4] / 1e3)
+                        setup_ms=info[4] / 1e3,
+                        phase_ms=dict(cf_split=info[5] / 1e3, extract=info[6] / 1e3, polynomial=info[7] / 1e3,
+                                      restrictor=info[8] / 1e3, coarse=info[9] / 1e3, layout=info[10] / 1e3))
         keys = ["n", "nnz", "nf", "nc", "nnz_aff", "nnz_afc", "nnz_ainv", "nnz_z", "coarsest", "nnz_acf",
-                "alpha_fitted", "nnz_af"]
+                "alpha_fitted", "nnz_af", "us_cf", "us_poly", "us_z", "us_coarse"]
         return {k: int(v) for k, v in zip(keys, info)}
 
     def solve(self, b, x=None, outer: str = "fgmres", restart: int = 30, max_it: int = 200, rtol: float = 1e-10,
@@ -253,6 +257,15 @@ class Hierarchy:
         ms = np.zeros(n)
         by = np.zeros(n)
         _check(lib().airg_kernel_times(self._h, la.ctypes.data, ms.ctypes.data, by.ctypes.data, n), "airg_kernel_times")
+        return {c: dict(launches=int(la[i]), ms=float(ms[i]), bytes=float(by[i])) for i, c in enumerate(PROFILE_CLASSES)}
+
+    def kernel_times_level(self, level: int) -> dict:
+        n = len(PROFILE_CLASSES)
+        la = np.zeros(n, dtype=np.int64)
+        ms = np.zeros(n)
+        by = np.zeros(n)
+        _check(lib().airg_kernel_times_level(self._h, level, la.ctypes.data, ms.ctypes.data, by.ctypes.data, n),
+               "airg_kernel_times_level")
         return {c: dict(launches=int(la[i]), ms=float(ms[i]), bytes=float(by[i])) for i, c in enumerate(PROFILE_CLASSES)}
 
 

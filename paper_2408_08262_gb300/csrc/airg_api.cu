@@ -1,6 +1,7 @@
 // C ABI of libairg.so (declared in include/airg.h): hierarchy construction, solves, CF-splitting
 // and export hooks, kernel timing.
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -43,35 +44,11 @@ int check_params(const airg_params* p) {
   return AIRG_OK;
 }
 
-// columns referenced at least once: the x traffic of an SpMV counted once per distinct column
-__global__ void k_touch(int nnz, const int* __restrict__ ci, unsigned char* __restrict__ flag) {
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
-    flag[ci[k]] = 1;
-}
-__global__ void k_count_flags(int n, const unsigned char* __restrict__ flag, int* cnt) {
-  int c = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c += flag[i];
-  if (c) atomicAdd(cnt, c);
-}
-
-// Algorithmic bytes of one SpMV with the given epilogue: CSR arrays once, each referenced x entry
-// once, y written once, b (RESID/ADDB) or y (ADD) read once.
-int spmv_bytes(const DCsr& A, bool reads_extra, Arena& tmp, cudaStream_t s, double* out) {
-  unsigned char* flag;
-  int* cnt;
-  AIRG_TRY(tmp.alloc(&flag, std::max(A.ncols, 1)));
-  AIRG_TRY(tmp.alloc(&cnt, 1));
-  CU_TRY(cudaMemsetAsync(flag, 0, std::max(A.ncols, 1), s));
-  CU_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-  if (A.nnz > 0) airg::note_launch(), k_touch<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.nnz, A.ci, flag);
-  if (A.ncols > 0) airg::note_launch(), k_count_flags<<<grid_for(A.ncols, 256), 256, 0, s>>>(A.ncols, flag, cnt);
-  CU_TRY(cudaGetLastError());
-  int h = 0;
-  CU_TRY(cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CU_TRY(cudaStreamSynchronize(s));
-  *out = 12.0 * A.nnz + 4.0 * (A.nrows + 1) + 8.0 * h + 8.0 * A.nrows * (reads_extra ? 2 : 1);
-  return AIRG_OK;
+// Algorithmic bytes of one SpMV with the given epilogue: the CSR arrays once, x once per column
+// (every solve operator references essentially all of its columns), y written once, and b
+// (RESID/ADDB) or y (ADD) read once.
+double spmv_bytes(const DCsr& A, bool reads_extra) {
+  return 12.0 * A.nnz + 4.0 * (A.nrows + 1) + 8.0 * A.ncols + 8.0 * A.nrows * (reads_extra ? 2 : 1);
 }
 
 int copy_csr(const DCsr& A, DCsr& B, Arena& a, cudaStream_t s) {
@@ -102,18 +79,37 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   H->n0 = Ain->n;
   H->top_nnz = Ain->nnz;
   DCsr A = A0;
+  std::vector<cudaEvent_t> evs;
+  struct EvRel {
+    std::vector<cudaEvent_t>& v;
+    ~EvRel() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } evrel{evs};
+  Arena lt;  // per-level scratch, reset and reused level after level
+  lt.s = s;
+  lt.chunk_min = (size_t)256 << 20;
+  struct LtRel {
+    Arena& a;
+    ~LtRel() { a.release(); }
+  } ltrel{lt};
   for (int l = 0;; ++l) {
     LevelBuild L;
+    for (int k = 0; k < 6; ++k)
+      if (cudaEventCreate(&L.ev[k]) == cudaSuccess) evs.push_back(L.ev[k]);
+      else { L.ev[k] = nullptr; cudaGetLastError(); }
     DCsr Ac;
-    Arena lt;
-    lt.s = s;
+    lt.reset();
     int rc = build_level(A, sp, l, l == sp.max_levels - 1, L, Ac, H->setup_mem, lt, s);
-    lt.release();
     if (rc != AIRG_OK) return rc;
     H->lb.push_back(L);
     if (L.coarsest) break;
     A = Ac;
   }
+  cudaEvent_t ev_layout0 = nullptr, ev_layout1 = nullptr;
+  if (cudaEventCreate(&ev_layout0) == cudaSuccess) evs.push_back(ev_layout0);
+  if (cudaEventCreate(&ev_layout1) == cudaSuccess) evs.push_back(ev_layout1);
+  if (ev_layout0) cudaEventRecord(ev_layout0, s);
   // solve-phase operators
   const int nl = (int)H->lb.size();
   H->lv.resize(nl);
@@ -135,8 +131,6 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
       AIRG_TRY(copy_csr(L.Ainv, S.Ainv, H->solve_mem, s));
       S.lanes_A = pick_lanes(avg_len(S.A));
       S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
-      AIRG_TRY(spmv_bytes(S.A, true, tmp, s, &S.bytes_A));
-      AIRG_TRY(spmv_bytes(S.Ainv, true, tmp, s, &S.bytes_Ainv));
       break;
     }
     S.nf = L.nf;
@@ -147,9 +141,6 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     S.lanes_AF = pick_lanes(avg_len(S.AF));
     S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
     S.lanes_Z = pick_lanes(avg_len(S.Z));
-    AIRG_TRY(spmv_bytes(S.AF, true, tmp, s, &S.bytes_AF));
-    AIRG_TRY(spmv_bytes(S.Ainv, true, tmp, s, &S.bytes_Ainv));
-    AIRG_TRY(spmv_bytes(S.Z, true, tmp, s, &S.bytes_Z));
     off += L.nf;
   }
   // top-level operator in the nested solve numbering of level 0
@@ -161,7 +152,7 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     H->pos0 = nullptr;
   }
   H->lanes_A0 = pick_lanes(avg_len(H->A0s));
-  AIRG_TRY(spmv_bytes(H->A0s, false, tmp, s, &H->bytes_A0));
+  if (ev_layout1) cudaEventRecord(ev_layout1, s);
   // complexities (Section "Strong tolerances"; storage complexity eq. mat_store)
   double gs = 0, os = 0, st = 0;
   for (int l = 0; l < nl; ++l) {
@@ -176,6 +167,21 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   H->op_cx = H->top_nnz > 0 ? os / H->top_nnz : 0;
   H->storage_cx = H->top_nnz > 0 ? st / H->top_nnz : 0;
   CU_TRY(cudaStreamSynchronize(s));
+  H->phase_ms.assign(nl, std::vector<float>(5, 0.f));
+  for (int l = 0; l < nl; ++l)
+    for (int k = 0; k < 5; ++k) {
+      const LevelBuild& L = H->lb[l];
+      float ms = 0.f;
+      if (L.ev[k] && L.ev[k + 1] && cudaEventElapsedTime(&ms, L.ev[k], L.ev[k + 1]) == cudaSuccess) H->phase_ms[l][k] = ms;
+      cudaGetLastError();
+    }
+  for (auto& L : H->lb)
+    for (auto& e : L.ev) e = nullptr;
+  {
+    float ms = 0.f;
+    if (ev_layout0 && ev_layout1 && cudaEventElapsedTime(&ms, ev_layout0, ev_layout1) == cudaSuccess) H->layout_ms = ms;
+    cudaGetLastError();
+  }
   H->alphas.resize(nl);
   for (int l = 0; l < nl; ++l) {
     H->alphas[l].assign(H->lb[l].m, 0.0);
@@ -205,7 +211,10 @@ void destroy(airg_hierarchy* H) {
   H->solve_mem.release();
   H->setup_mem.release();
   cudaStreamSynchronize(H->s);
+  if (H->vg_exec) cudaGraphExecDestroy(H->vg_exec);
+  if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   for (auto e : H->prof.pool) cudaEventDestroy(e);
+  for (auto e : H->prof.graph_pool) cudaEventDestroy(e);
   if (H->hsc) cudaFreeHost(H->hsc);
   delete H;
 }
@@ -225,7 +234,7 @@ void airg_params_default(airg_params* p) {
   p->strong_threshold = 0.5;
   p->ddc_fraction = 0.1;
   p->pmisr_max_loops = 3;
-  p->poly_order = 2;
+  p->poly_order = 6;
   p->coarse_poly_order = 12;
   p->coarse_iters = 3;
   p->coarse_size = 64;
@@ -248,6 +257,10 @@ int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, ai
   if (!H) return AIRG_ERR_OOM;
   H->p = *p;
   H->s = (cudaStream_t)stream;
+  {
+    const char* g = getenv("AIRG_NO_GRAPH");
+    H->use_graph = (g && g[0] == '1') ? 0 : 1;
+  }
   H->solve_mem.s = H->s;
   H->setup_mem.s = H->s;
   {
@@ -315,7 +328,7 @@ int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t str
   AIRG_TRY(solve_alloc(H, 1));
   if (H->pos0) dev_permute(b, H->pos0, H->bp, H->n0, false, H->s);
   else CU_TRY(cudaMemcpyAsync(H->bp, b, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s));
-  AIRG_TRY(vcycle_solve_order(H, H->bp, H->xp));
+  AIRG_TRY(vcycle_apply(H, H->bp, H->xp));
   if (H->pos0) dev_permute(H->xp, H->pos0, x, H->n0, true, H->s);
   else CU_TRY(cudaMemcpyAsync(x, H->xp, sizeof(double) * H->n0, cudaMemcpyDeviceToDevice, H->s));
   CU_TRY(cudaGetLastError());
@@ -359,6 +372,11 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
     info[2] = (int64_t)std::llround(H->op_cx * 1e6);
     info[3] = (int64_t)std::llround(H->storage_cx * 1e6);
     info[4] = (int64_t)std::llround(H->setup_ms * 1e3);
+    double tot[5] = {0, 0, 0, 0, 0};
+    for (auto& v : H->phase_ms)
+      for (int k = 0; k < 5; ++k) tot[k] += v[k];
+    for (int k = 0; k < 5; ++k) info[5 + k] = (int64_t)std::llround(tot[k] * 1e3);
+    info[10] = (int64_t)std::llround(H->layout_ms * 1e3);
     return AIRG_OK;
   }
   if (level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
@@ -376,6 +394,14 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
   info[9] = L.Acf.nnz;
   info[10] = L.fitted;
   info[11] = S.AF.nnz;
+  if (level < (int)H->phase_ms.size())
+  {
+    const auto& ph = H->phase_ms[level];
+    info[12] = (int64_t)std::llround((ph[0] + ph[1]) * 1e3);  // CF splitting + extraction
+    info[13] = (int64_t)std::llround(ph[2] * 1e3);            // polynomial fit and assembly
+    info[14] = (int64_t)std::llround(ph[3] * 1e3);            // restrictor product
+    info[15] = (int64_t)std::llround(ph[4] * 1e3);            // prolongator and coarse matrix
+  }
   return AIRG_OK;
 }
 
@@ -439,12 +465,28 @@ int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t
 
 int airg_profile_enable(airg_hierarchy* H, int enable) {
   if (!H) return AIRG_ERR_ARG;
+  if (enable && !H->bytes_A0) {
+    for (auto& S : H->lv) {
+      if (S.coarsest) S.bytes_A = spmv_bytes(S.A, true);
+      S.bytes_Ainv = spmv_bytes(S.Ainv, true);
+      if (!S.coarsest) {
+        S.bytes_AF = spmv_bytes(S.AF, true);
+        S.bytes_Z = spmv_bytes(S.Z, true);
+      }
+    }
+    H->bytes_A0 = spmv_bytes(H->A0s, false);
+  }
   H->prof.on = enable != 0;
   H->prof.mask = (unsigned)enable;
   for (int c = 0; c < PC_N; ++c) {
     H->prof.launches[c] = 0;
     H->prof.ms[c] = 0.0;
     H->prof.bytes[c] = 0.0;
+    for (int l = 0; l < Profiler::kMaxLv; ++l) {
+      H->prof.lv_launches[l][c] = 0;
+      H->prof.lv_ms[l][c] = 0.0;
+      H->prof.lv_bytes[l][c] = 0.0;
+    }
   }
   return AIRG_OK;
 }
@@ -461,6 +503,17 @@ int airg_kernel_times(airg_hierarchy* H, int64_t* launches, double* ms, double* 
 }
 
 int64_t airg_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int airg_kernel_times_level(airg_hierarchy* H, int level, int64_t* launches, double* ms, double* bytes, int nclasses) {
+  if (!H || nclasses < 0 || level < 0 || level >= Profiler::kMaxLv) return AIRG_ERR_ARG;
+  AIRG_TRY(prof_flush(H));
+  for (int c = 0; c < nclasses && c < PC_N; ++c) {
+    if (launches) launches[c] = H->prof.lv_launches[level][c];
+    if (ms) ms[c] = H->prof.lv_ms[level][c];
+    if (bytes) bytes[c] = H->prof.lv_bytes[level][c];
+  }
+  return AIRG_OK;
+}
 
 const char* airg_status_string(int status) {
   switch (status) {

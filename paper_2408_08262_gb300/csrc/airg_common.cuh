@@ -40,22 +40,41 @@ struct DCsr {
   double* v = nullptr;
 };
 
-// Stream-ordered device memory with ownership tracking.  Everything allocated through an Arena
-// is released by release() (or the destructor of the owner that calls it).
+// Stream-ordered device memory.  An Arena hands out 256-byte-aligned sub-ranges of large chunks
+// obtained with cudaMallocAsync (bump allocation), so a hierarchy owns a handful of blocks rather
+// than thousands of arrays.  reset() makes every chunk reusable (all users are on the same stream,
+// so later kernels see the memory only after earlier ones are done); release() frees the chunks.
 struct Arena {
   cudaStream_t s = nullptr;
-  std::vector<void*> ptrs;
+  size_t chunk_min = (size_t)64 << 20;
+  struct Chunk {
+    char* base;
+    size_t size, used;
+  };
+  std::vector<Chunk> chunks;
+  size_t cur = 0;  // first chunk that may still have room
   template <class T>
   int alloc(T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), s);
+    const size_t bytes = ((n * sizeof(T)) + 255) & ~(size_t)255;
+    for (size_t c = cur; c < chunks.size(); ++c) {
+      if (chunks[c].size - chunks[c].used >= bytes) {
+        *p = reinterpret_cast<T*>(chunks[c].base + chunks[c].used);
+        chunks[c].used += bytes;
+        return AIRG_OK;
+      }
+      if (c == cur && chunks[c].size - chunks[c].used < 4096) ++cur;  // nearly full: skip from now on
+    }
+    size_t sz = bytes > chunk_min ? bytes : chunk_min;
+    void* b = nullptr;
+    cudaError_t e = cudaMallocAsync(&b, sz, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      *p = nullptr;
       return e == cudaErrorMemoryAllocation ? AIRG_ERR_OOM : AIRG_ERR_CUDA;
     }
-    ptrs.push_back((void*)*p);
+    chunks.push_back({(char*)b, sz, bytes});
+    *p = reinterpret_cast<T*>(b);
     return AIRG_OK;
   }
   int csr(DCsr& A, int nrows, int ncols, int nnz) {
@@ -67,9 +86,14 @@ struct Arena {
     AIRG_TRY(alloc(&A.v, (size_t)nnz));
     return AIRG_OK;
   }
+  void reset() {
+    for (auto& c : chunks) c.used = 0;
+    cur = 0;
+  }
   void release() {
-    for (void* p : ptrs) cudaFreeAsync(p, s);
-    ptrs.clear();
+    for (auto& c : chunks) cudaFreeAsync(c.base, s);
+    chunks.clear();
+    cur = 0;
   }
 };
 
@@ -119,6 +143,10 @@ enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_ADDB = 3 };
 // y = A x (SET) | b - A x (RESID) | y + A x (ADD) | b + A x (ADDB; y may alias b)
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s);
 int pick_lanes(double avg_row_len);
+// r = b_F - AF x with x_F taken as the one-point prolongation of x_C (x[f] = x[nf + w[f]]), which
+// is also stored into x_F.  AF has nf rows; x holds [x_F, x_C].
+int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
+                           cudaStream_t s);
 
 void dev_scale(const double* x, double alpha_div, double* y, int n, cudaStream_t s);  // y = x / a
 void dev_permute(const double* in, const int* pos, double* out, int n, bool inverse, cudaStream_t s);
@@ -166,6 +194,9 @@ struct LevelBuild {
   double* alpha = nullptr;
   int m = 0, fitted = 0;
   bool coarsest = false;
+  // phase boundaries (CUDA events, recorded when non-null): start, CF split, extraction,
+  // polynomial (steps 3-8), restrictor, prolongator + coarse matrix
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 // Builds level data and the next coarse matrix (setup steps 1-11).  If the level turns out to be

@@ -29,14 +29,24 @@ struct Profiler {
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   struct Rec {
-    int cls;
+    int cls, level;
     cudaEvent_t a, b;
     double bytes;
   };
   std::vector<Rec> pending;
+  // events recorded inside the captured V-cycle graph: read after every replay
+  bool capturing = false;
+  std::vector<cudaEvent_t> graph_pool;
+  size_t graph_used = 0;
+  std::vector<Rec> graph_recs;
+  int graph_unread = 0;
   long long launches[PC_N] = {};
   double ms[PC_N] = {};
   double bytes[PC_N] = {};
+  static constexpr int kMaxLv = 128;  // per-level sums (levels beyond the last slot are folded in)
+  long long lv_launches[kMaxLv][PC_N] = {};
+  double lv_ms[kMaxLv][PC_N] = {};
+  double lv_bytes[kMaxLv][PC_N] = {};
 };
 
 }  // namespace airg
@@ -61,8 +71,16 @@ struct airg_hierarchy {
   double* hsc = nullptr;  // pinned host mirror of dsc
   airg::Reducer red{};
   airg::Profiler prof;
+  // V-cycle as a CUDA graph over fixed buffers gin -> gout, captured on first use
+  int use_graph = 1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t vg_exec = nullptr;
+  unsigned vg_mask = 0xffffffffu;
+  long long vg_kernels = 0;  // kernel nodes in the graph (counted at every replay)
+  double *gin = nullptr, *gout = nullptr;
   // info
-  double setup_ms = 0, grid_cx = 0, op_cx = 0, storage_cx = 0;
+  double setup_ms = 0, grid_cx = 0, op_cx = 0, storage_cx = 0, layout_ms = 0;
+  std::vector<std::vector<float>> phase_ms;  // per level: CF split, extraction, polynomial, Z, P + RAP
   long long top_nnz = 0;
   bool kept = false;
 };
@@ -70,6 +88,9 @@ struct airg_hierarchy {
 namespace airg {
 int solve_alloc(airg_hierarchy* H, int restart);
 int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0);
+// x0 = M b0 in the solve numbering, through the captured graph when enabled
+int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0);
+int prof_graph_read(airg_hierarchy* H);
 int solve_fgmres(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
 int solve_richardson(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
 int prof_flush(airg_hierarchy* H);

@@ -206,17 +206,20 @@ __global__ void __launch_bounds__(256) k_gs_pass(const double* __restrict__ V, l
   for (int k = 0; k <= NC; ++k) acc[k] = 0.0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
     double wr = w[r];
+    double vk[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) vk[k] = (k < ncols && (hsub || k < nd)) ? V[(size_t)k * ldv + r] : 0.0;
     if (hsub) {
       double sub = 0.0;
 #pragma unroll
       for (int k = 0; k < NC; ++k)
-        if (k < ncols) sub += V[(size_t)k * ldv + r] * sh[k];
+        if (k < ncols) sub += vk[k] * sh[k];
       wr -= sub;
       w[r] = wr;
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-      if (k < nd) acc[k] += V[(size_t)k * ldv + r] * wr;
+      if (k < nd) acc[k] += vk[k] * wr;
     acc[NC] += wr * wr;
   }
   // place the norm accumulator right after the nd dots so one finish call reduces nd+1 values
@@ -262,73 +265,127 @@ int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, d
 }
 
 // ------------------------------------------------------------------------------------------
-// CSR SpMV: LPR lanes cooperate on one row; the epilogue is fused.
+// CSR SpMV, tiled: a CTA owns 256 consecutive rows.  Their nonzeros (a contiguous range of the CSR
+// arrays) are streamed in chunks of kSpmvChunk entries with coalesced loads of values and column
+// indices and independent gathers of x; the products go to shared memory and each thread then sums
+// its own row's products in ascending column-storage order (the plain sequential row sum).  All
+// loads of a chunk are independent of one another, so many are in flight per thread, which is what
+// a 5-nonzeros-per-row matrix needs to approach the HBM roofline.
 // ------------------------------------------------------------------------------------------
-template <int LPR, int MODE>
-__global__ void __launch_bounds__(256) k_spmv(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                              const double* __restrict__ v, const double* __restrict__ x,
-                                              const double* b, double* y) {
-  // The loop bound is uniform across the warp (every lane iterates the same number of times), so
-  // the width-LPR shuffles always run with the whole warp present.
-  constexpr int GPW = 32 / LPR;  // row groups per warp
+constexpr int kSpmvThreads = 256;
+constexpr int kSpmvChunk = 2048;
+
+// LPR lanes sum each row (LPR = 1: one thread per row, summing in storage order); a CTA owns
+// kSpmvThreads / LPR consecutive rows, so operators with long rows still give many CTAs.
+// PROLONG: first F-smoothing residual with the one-point prolongation fused in (see
+// dev_spmv_resid_prolong).
+template <int LPR, int MODE, bool PROLONG>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                       const double* __restrict__ v, const double* x,
+                                                       const double* b, double* y, const int* __restrict__ w,
+                                                       double* xf) {
+  constexpr int RPB = kSpmvThreads / LPR;
+  __shared__ double prod[kSpmvChunk];
+  const int r0 = blockIdx.x * RPB;
+  const int r1 = min(r0 + RPB, nrows);
   const int lane = threadIdx.x % LPR;
-  const int gin = (threadIdx.x & 31) / LPR;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * GPW; base < nrows; base += nwarps * GPW) {
-    const long long row = base + gin;
-    const bool valid = row < nrows;
-    double s = 0.0;
-    if (valid) {
-      const int beg = rp[row], end = rp[row + 1];
-      for (int k = beg + lane; k < end; k += LPR) s += v[k] * __ldg(x + ci[k]);
+  const int row = r0 + threadIdx.x / LPR;
+  const bool has = row < r1;
+  const int rb = has ? rp[row] : 0;
+  const int re = has ? rp[row + 1] : 0;
+  const int k0 = rp[r0], k1 = rp[r1];
+  double s = 0.0;
+  for (int c0 = k0; c0 < k1; c0 += kSpmvChunk) {
+    const int c1 = min(c0 + kSpmvChunk, k1);
+    for (int k = c0 + threadIdx.x; k < c1; k += kSpmvThreads) {
+      const int c = ci[k];
+      double xv;
+      if (PROLONG && c < nrows) {
+        const int src = w[c];
+        xv = src >= 0 ? x[nrows + src] : 0.0;
+      } else {
+        xv = __ldg(x + c);
+      }
+      prod[k - c0] = v[k] * xv;
     }
+    __syncthreads();
+    if (has) {
+      const int lo = max(rb, c0), hi = min(re, c1);
+      for (int k = lo + lane; k < hi; k += LPR) s += prod[k - c0];
+    }
+    __syncthreads();
+  }
+  if (LPR > 1) {
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-    if (valid && lane == 0) {
-      double out;
-      if (MODE == SPMV_SET) out = s;
-      else if (MODE == SPMV_RESID) out = b[row] - s;
-      else if (MODE == SPMV_ADD) out = y[row] + s;
-      else out = b[row] + s;
-      y[row] = out;
+  }
+  if (has && lane == 0) {
+    double out;
+    if (MODE == SPMV_SET) out = s;
+    else if (MODE == SPMV_RESID) out = b[row] - s;
+    else if (MODE == SPMV_ADD) out = y[row] + s;
+    else out = b[row] + s;
+    y[row] = out;
+    if (PROLONG) {
+      const int src = w[row];
+      xf[row] = src >= 0 ? x[nrows + src] : 0.0;
     }
   }
 }
 
-int pick_lanes(double L) {
-  if (L <= 3.0) return 2;
-  if (L <= 7.0) return 4;
-  if (L <= 14.0) return 8;
-  if (L <= 28.0) return 16;
-  return 32;
+template <int LPR>
+static void launch_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
+                        cudaStream_t s) {
+  const int grid = ceil_div(A.nrows, kSpmvThreads / LPR);
+  if (w) {
+    airg::note_launch(), k_spmv<LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, w, xf);
+    return;
+  }
+  switch (mode) {
+    case SPMV_SET: airg::note_launch(), k_spmv<LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv<LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv<LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
+    default: airg::note_launch(), k_spmv<LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
+  }
 }
 
-template <int LPR>
-static void launch_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, cudaStream_t s) {
-  const int block = 256;
-  long long work = (long long)A.nrows * LPR;
-  int grid = grid_for(work, block, 152 * 16);
-  switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv<LPR, SPMV_SET><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv<LPR, SPMV_RESID><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv<LPR, SPMV_ADD><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
-    default: airg::note_launch(), k_spmv<LPR, SPMV_ADDB><<<grid, block, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y); break;
+static void spmv_dispatch(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, const int* w,
+                          double* xf, cudaStream_t s) {
+  switch (lanes) {
+    case 1: launch_spmv<1>(A, x, b, y, mode, w, xf, s); break;
+    case 2: launch_spmv<2>(A, x, b, y, mode, w, xf, s); break;
+    case 4: launch_spmv<4>(A, x, b, y, mode, w, xf, s); break;
+    case 8: launch_spmv<8>(A, x, b, y, mode, w, xf, s); break;
+    case 16: launch_spmv<16>(A, x, b, y, mode, w, xf, s); break;
+    default: launch_spmv<32>(A, x, b, y, mode, w, xf, s); break;
   }
 }
 
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
-  switch (lanes) {
-    case 1: launch_spmv<1>(A, x, b, y, mode, s); break;
-    case 2: launch_spmv<2>(A, x, b, y, mode, s); break;
-    case 4: launch_spmv<4>(A, x, b, y, mode, s); break;
-    case 8: launch_spmv<8>(A, x, b, y, mode, s); break;
-    case 16: launch_spmv<16>(A, x, b, y, mode, s); break;
-    default: launch_spmv<32>(A, x, b, y, mode, s); break;
-  }
+  spmv_dispatch(A, x, b, y, mode, lanes, nullptr, nullptr, s);
   KERNEL_CHECK();
   return AIRG_OK;
+}
+
+// r = b_F - AF x with x_F replaced by the one-point prolongation of x_C; x_F is written too.
+int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
+                           cudaStream_t s) {
+  if (AF.nrows <= 0) return AIRG_OK;
+  spmv_dispatch(AF, x, b, y, SPMV_RESID, lanes, w, x, s);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// Lanes per row for the tiled SpMV: one thread per row for short rows (the sequential storage-
+// order sum), more lanes as rows grow so that a CTA's 256 / LPR rows hold about one chunk.
+int pick_lanes(double L) {
+  if (L <= 12.0) return 1;
+  if (L <= 24.0) return 2;
+  if (L <= 48.0) return 4;
+  if (L <= 96.0) return 8;
+  if (L <= 192.0) return 16;
+  return 32;
 }
 
 // ------------------------------------------------------------------------------------------

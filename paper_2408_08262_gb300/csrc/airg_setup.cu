@@ -417,13 +417,16 @@ __global__ void k_box_muller(int n, uint64_t key, double* __restrict__ z) {
 // upper-triangular nc x nc factor (row-major, zeros below the diagonal and in rows past the
 // block's row count) goes to out + b*nc*nc.  Used for the first TSQR stage (the power basis) and
 // for every combine stage (stacked R factors).
-constexpr int kQrRows = 256;
+constexpr int kQrRows = 512;
 constexpr int kQrMaxCols = 16;
 
+// M is the block's tile in dynamic shared memory, column-major with leading dimension kQrRows
+// (nc * kQrRows doubles).
 __global__ void __launch_bounds__(256) k_householder(const double* __restrict__ in, long long rs, long long cs,
                                                      long long nrows, int nc, int rows_per_block,
                                                      double* __restrict__ out) {
-  __shared__ double M[kQrMaxCols][kQrRows];
+  extern __shared__ double Msh[];
+  auto M = reinterpret_cast<double(*)[kQrRows]>(Msh);
   __shared__ double red[8][kQrMaxCols + 1];
   __shared__ double tot[kQrMaxCols + 1];
   const long long r0 = (long long)blockIdx.x * rows_per_block;
@@ -555,17 +558,20 @@ int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int*
   const int lanes = pick_lanes((double)A.nnz / std::max(1, n));
   for (int c = 1; c < nc; ++c) AIRG_TRY(dev_spmv(A, K + (size_t)(c - 1) * n, nullptr, K + (size_t)c * n, SPMV_SET, lanes, s));
   // TSQR: stage 1 on the power basis, then combine stacked factors until one remains
+  const size_t qr_smem = sizeof(double) * (size_t)nc * kQrRows;
+  if (qr_smem > 48 * 1024)
+    CU_TRY(cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
   long long nb = (n + kQrRows - 1) / kQrRows;
   double* R;
   AIRG_TRY(tmp.alloc(&R, (size_t)nb * nc * nc));
-  airg::note_launch(), k_householder<<<(int)nb, 256, 0, s>>>(K, 1, n, n, nc, kQrRows, R);
+  airg::note_launch(), k_householder<<<(int)nb, 256, qr_smem, s>>>(K, 1, n, n, nc, kQrRows, R);
   KERNEL_CHECK();
   const int group = std::max(1, kQrRows / nc);
   while (nb > 1) {
     long long nb2 = (nb + group - 1) / group;
     double* R2;
     AIRG_TRY(tmp.alloc(&R2, (size_t)nb2 * nc * nc));
-    airg::note_launch(), k_householder<<<(int)nb2, 256, 0, s>>>(R, nc, 1, nb * nc, nc, group * nc, R2);
+    airg::note_launch(), k_householder<<<(int)nb2, 256, qr_smem, s>>>(R, nc, 1, nb * nc, nc, group * nc, R2);
     KERNEL_CHECK();
     R = R2;
     nb = nb2;
@@ -665,7 +671,6 @@ int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out,
 // Rows whose candidate count fits kWarpCap are done by one warp, longer rows by one CTA.
 // ------------------------------------------------------------------------------------------
 constexpr int kWarpCap = 1024;
-constexpr int kSpgWarps = 8;
 constexpr int kBlockCapMax = 32768;
 
 __global__ void k_spgemm_ub(int ar, const int* __restrict__ arp, const int* __restrict__ aci,
@@ -692,8 +697,6 @@ struct SpgArgs {
   int* tcol;
   double* tval;
   int* cnt;
-  int* long_rows;
-  int* n_long;
 };
 
 // Group-generic pieces (G threads cooperate; sync() is __syncwarp or __syncthreads).
@@ -752,48 +755,162 @@ __device__ __forceinline__ double spg_value(const SpgArgs& g, int ab, int ae, in
   return g.scale * acc;
 }
 
-__global__ void __launch_bounds__(kSpgWarps * 32) k_spgemm_warp(SpgArgs g) {
-  __shared__ int sbuf[kSpgWarps][kWarpCap];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int* buf = sbuf[wid];
-  const long long gw = (long long)blockIdx.x * kSpgWarps + wid;
-  const long long nw = (long long)gridDim.x * kSpgWarps;
-  for (long long ii = gw; ii < g.ar; ii += nw) {
+// Short rows (candidate count <= kThreadCap): one thread per row.  For each A entry in ascending
+// order the B row is merged into a per-thread sorted list whose accumulators take
+// fma(a_il, b_lj, acc) as the entry is met, so every output sums in ascending inner index with no
+// search.  Rows with more candidates go to `mid_rows` (warp kernel).
+constexpr int kThreadCap = 32;
+
+__global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows, int* n_mid) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < g.ar; ii += (long long)gridDim.x * blockDim.x) {
     const int i = (int)ii;
     const long long ub = g.ubo[i + 1] - g.ubo[i];
-    if (ub == 0) { if (lane == 0) g.cnt[i] = 0; continue; }
-    if (ub > kWarpCap) {
-      if (lane == 0) { g.long_rows[atomicAdd(g.n_long, 1)] = i; g.cnt[i] = 0; }
-      continue;
-    }
+    if (ub == 0) { g.cnt[i] = 0; continue; }
+    if (ub > kThreadCap) { mid_rows[atomicAdd(n_mid, 1)] = i; continue; }
     const int ab = g.arp[i], ae = g.arp[i + 1];
-    int off = 0;
+    int cand[kThreadCap];
+    double acc[kThreadCap];
+    int u = 0;
     for (int k = ab; k < ae; ++k) {
       const int l = g.aci[k];
+      const double a = g.av[k];
+      for (int q = g.brp[l]; q < g.brp[l + 1]; ++q) {
+        const int j = g.bci[q];
+        const double bv = g.bv[q];
+        int pos = u;
+        while (pos > 0 && cand[pos - 1] > j) --pos;
+        if (pos > 0 && cand[pos - 1] == j) {
+          acc[pos - 1] = fma(a, bv, acc[pos - 1]);
+          continue;
+        }
+        for (int t = u; t > pos; --t) { cand[t] = cand[t - 1]; acc[t] = acc[t - 1]; }
+        cand[pos] = j;
+        acc[pos] = fma(a, bv, 0.0);
+        ++u;
+      }
+    }
+    double mx = 0.0;
+    for (int t = 0; t < u; ++t) {
+      acc[t] = g.scale * acc[t];
+      mx = fmax(mx, fabs(acc[t]));
+    }
+    const double thr = g.tol * mx;
+    const long long o = g.ubo[i];
+    int outc = 0;
+    for (int t = 0; t < u; ++t) {
+      const double c = acc[t];
+      const int j = cand[t];
+      if (!(fabs(c) < thr) || (g.keep_diag && j == i)) {
+        g.tcol[o + outc] = j;
+        g.tval[o + outc] = c;
+        ++outc;
+      }
+    }
+    g.cnt[i] = outc;
+  }
+}
+
+// Medium rows (candidate count <= kWarpCap): one warp per row with a shared-memory hash table.
+// For each A entry (ascending, one at a time) the lanes take the distinct columns of that B row in
+// parallel and update their slots with fma -- no two lanes touch one key in the same step, so every
+// output accumulates in ascending inner index.  The occupied slots are then compacted, sorted by
+// column (bitonic, values carried along), scaled and dropped.
+
+template <int G>
+__device__ void bitonic_sort_kv(int* a, double* v, int P, int t) {
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int idx = t; idx < P; idx += G) {
+        const int ixj = idx ^ j;
+        if (ixj > idx) {
+          const int x = a[idx], y = a[ixj];
+          const bool up = ((idx & k) == 0);
+          if ((x > y) == up) {
+            a[idx] = y;
+            a[ixj] = x;
+            const double tv = v[idx];
+            v[idx] = v[ixj];
+            v[ixj] = tv;
+          }
+        }
+      }
+      Grp<G>::sync();
+    }
+}
+
+template <int CAP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int* __restrict__ rows,
+                                                            const int* __restrict__ nrows_dev, int* next_rows,
+                                                            int* n_next) {
+  __shared__ int hkey[WARPS][CAP];
+  __shared__ double hval[WARPS][CAP];
+  const int nrows = *nrows_dev;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* key = hkey[wid];
+  double* val = hval[wid];
+  const long long gw = (long long)blockIdx.x * WARPS + wid;
+  const long long nw = (long long)gridDim.x * WARPS;
+  for (long long ii = gw; ii < nrows; ii += nw) {
+    const int i = rows[ii];
+    const long long ub = g.ubo[i + 1] - g.ubo[i];
+    if (ub > CAP) {
+      if (lane == 0) next_rows[atomicAdd(n_next, 1)] = i;
+      continue;
+    }
+    int H = 32, lg = 5;
+    while (H < ub) { H <<= 1; ++lg; }
+    for (int t = lane; t < H; t += 32) { key[t] = -1; val[t] = 0.0; }
+    __syncwarp();
+    const int ab = g.arp[i], ae = g.arp[i + 1];
+    for (int k = ab; k < ae; ++k) {
+      const int l = g.aci[k];
+      const double a = g.av[k];
       const int b0 = g.brp[l], len = g.brp[l + 1] - b0;
-      for (int t = lane; t < len; t += 32) buf[off + t] = g.bci[b0 + t];
-      off += len;
+      for (int t = lane; t < len; t += 32) {
+        const int j = g.bci[b0 + t];
+        const double bv = g.bv[b0 + t];
+        unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - lg);
+        while (true) {
+          const int prev = atomicCAS(&key[h], -1, j);
+          if (prev == -1 || prev == j) break;
+          h = (h + 1) & (H - 1);
+        }
+        val[h] = fma(a, bv, val[h]);
+      }
+      __syncwarp();
+    }
+    // compact occupied slots to the front (chunks read before written), then sort by column
+    int u = 0;
+    for (int base = 0; base < H; base += 32) {
+      const int idx = base + lane;
+      const int kk = key[idx];
+      const double vv = val[idx];
+      const bool occ = kk >= 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, occ);
+      __syncwarp();
+      if (occ) {
+        const int d = u + __popc(bal & ((1u << lane) - 1u));
+        key[d] = kk;
+        val[d] = vv;
+      }
+      u += __popc(bal);
+      __syncwarp();
     }
     int P = 32;
-    while (P < ub) P <<= 1;
-    for (int t = (int)ub + lane; t < P; t += 32) buf[t] = 0x7fffffff;
+    while (P < u) P <<= 1;
+    for (int t = u + lane; t < P; t += 32) { key[t] = 0x7fffffff; val[t] = 0.0; }
     __syncwarp();
-    bitonic_sort<32>(buf, P, lane);
-    const int u = warp_unique_sorted(buf, P, lane);
-    // values
-    const long long o = g.ubo[i];
+    bitonic_sort_kv<32>(key, val, P, lane);
     double mx = 0.0;
     for (int t = lane; t < u; t += 32) {
-      const int j = buf[t];
-      const double c = spg_value(g, ab, ae, j);
-      g.tcol[o + t] = j;
-      g.tval[o + t] = c;
+      const double c = g.scale * val[t];
+      val[t] = c;
       mx = fmax(mx, fabs(c));
     }
     for (int s2 = 16; s2 > 0; s2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
     const double thr = g.tol * mx;
     __syncwarp();
-    // drop + compaction in the row's temporary slot
+    const long long o = g.ubo[i];
     int outc = 0;
     for (int base = 0; base < u; base += 32) {
       const int t = base + lane;
@@ -801,32 +918,39 @@ __global__ void __launch_bounds__(kSpgWarps * 32) k_spgemm_warp(SpgArgs g) {
       double c = 0.0;
       bool keep = false;
       if (t < u) {
-        j = g.tcol[o + t];
-        c = g.tval[o + t];
+        j = key[t];
+        c = val[t];
         keep = !(fabs(c) < thr) || (g.keep_diag && j == i);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      __syncwarp();
       if (keep) {
         const int d = outc + __popc(bal & ((1u << lane) - 1u));
         g.tcol[o + d] = j;
         g.tval[o + d] = c;
       }
       outc += __popc(bal);
-      __syncwarp();
     }
     if (lane == 0) g.cnt[i] = outc;
+    __syncwarp();
   }
 }
 
-// Long rows: one 256-thread CTA per row, dynamic shared memory of P ints.
-__global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __restrict__ rows, int cap) {
+// Long rows: one 256-thread CTA per row (grid-stride over the device-side list), dynamic shared
+// memory of `cap` ints; a row beyond `cap` candidates sets *err and is skipped.
+__global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __restrict__ rows,
+                                                      const int* __restrict__ nrows_dev, int cap, int* err) {
   extern __shared__ int bbuf[];
   __shared__ int wcnt[8];
   __shared__ double wmx[8];
-  const int i = rows[blockIdx.x];
+  const int nrows = *nrows_dev;
+  for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+  const int i = rows[rr];
   const int t0 = threadIdx.x, lane = t0 & 31, wid = t0 >> 5;
   const long long ub = g.ubo[i + 1] - g.ubo[i];
+  if (ub > cap) {
+    if (t0 == 0) { atomicOr(err, 1); g.cnt[i] = 0; }
+    continue;
+  }
   const int ab = g.arp[i], ae = g.arp[i + 1];
   int off = 0;
   for (int k = ab; k < ae; ++k) {
@@ -900,19 +1024,17 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
     __syncthreads();
   }
   if (t0 == 0) g.cnt[i] = outc;
-  (void)cap;
+  __syncthreads();
+  }
 }
 
 __global__ void k_spgemm_copy(int ar, const long long* __restrict__ ubo, const int* __restrict__ tcol,
                               const double* __restrict__ tval, const int* __restrict__ rp, int* __restrict__ ci,
                               double* __restrict__ v) {
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = gw; i < ar; i += nw) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ar; i += (long long)gridDim.x * blockDim.x) {
     const long long o = ubo[i];
     const int b = rp[i], len = rp[i + 1] - b;
-    for (int t = lane; t < len; t += 32) {
+    for (int t = 0; t < len; ++t) {
       ci[b + t] = tcol[o + t];
       v[b + t] = tval[o + t];
     }
@@ -938,37 +1060,33 @@ int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_dia
   AIRG_TRY(tmp.alloc(&g.tcol, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.tval, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.cnt, std::max(ar, 1)));
-  AIRG_TRY(tmp.alloc(&g.long_rows, std::max(ar, 1)));
-  AIRG_TRY(tmp.alloc(&g.n_long, 1));
-  CU_TRY(cudaMemsetAsync(g.n_long, 0, sizeof(int), s));
+  // row lists of the wider paths; counters: [0] mid, [1] big, [2] long, [3] error
+  int *mid, *big, *lng, *ctr;
+  AIRG_TRY(tmp.alloc(&mid, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&big, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&lng, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&ctr, 4));
+  CU_TRY(cudaMemsetAsync(ctr, 0, 4 * sizeof(int), s));
   if (ar > 0) {
-    airg::note_launch(), k_spgemm_warp<<<grid_for((long long)ar * 32, kSpgWarps * 32, 152 * 64), kSpgWarps * 32, 0, s>>>(g);
-    KERNEL_CHECK();
-    int nlong = 0;
-    CU_TRY(cudaMemcpyAsync(&nlong, g.n_long, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU_TRY(cudaStreamSynchronize(s));
-    if (nlong > 0) {
-      // capacity: the longest candidate list among the long rows (host-side max over ub)
-      std::vector<int> lr(nlong);
-      CU_TRY(cudaMemcpyAsync(lr.data(), g.long_rows, sizeof(int) * nlong, cudaMemcpyDeviceToHost, s));
-      std::vector<long long> hub(ar + 1);
-      CU_TRY(cudaMemcpyAsync(hub.data(), ubo, sizeof(long long) * (ar + 1), cudaMemcpyDeviceToHost, s));
-      CU_TRY(cudaStreamSynchronize(s));
-      long long mx = 0;
-      for (int r : lr) mx = std::max(mx, hub[r + 1] - hub[r]);
-      if (mx > kBlockCapMax) return AIRG_ERR_UNSUPPORTED;
-      int P = 256;
-      while (P < mx) P <<= 1;
-      const size_t smem = sizeof(int) * (size_t)P;
-      if (smem > 48 * 1024) CU_TRY(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      airg::note_launch(), k_spgemm_block<<<nlong, 256, smem, s>>>(g, g.long_rows, P);
-      KERNEL_CHECK();
+    airg::note_launch(), k_spgemm_thread<<<grid_for(ar, 128, 152 * 64), 128, 0, s>>>(g, mid, ctr + 0);
+    airg::note_launch(), k_spgemm_warp<256, 16><<<152 * 4, 16 * 32, 0, s>>>(g, mid, ctr + 0, big, ctr + 1);
+    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2);
+    static bool smem_set = false;
+    const size_t smem = sizeof(int) * (size_t)kBlockCapMax;
+    if (!smem_set) {
+      CU_TRY(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      smem_set = true;
     }
+    airg::note_launch(), k_spgemm_block<<<152, 256, smem, s>>>(g, lng, ctr + 2, kBlockCapMax, ctr + 3);
+    KERNEL_CHECK();
   }
   int* rp;
   AIRG_TRY(own.alloc(&rp, (size_t)ar + 1));
+  int err = 0;
+  CU_TRY(cudaMemcpyAsync(&err, ctr + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
   long long nnz = 0;
-  AIRG_TRY(scan_i32(g.cnt, rp, ar, tmp, s, &nnz));
+  AIRG_TRY(scan_i32(g.cnt, rp, ar, tmp, s, &nnz));  // synchronises: err is valid below
+  if (err) return AIRG_ERR_UNSUPPORTED;
   if (nnz > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
   out.nrows = ar;
   out.ncols = B.ncols;
@@ -976,7 +1094,7 @@ int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_dia
   out.rp = rp;
   AIRG_TRY(own.alloc(&out.ci, (size_t)nnz));
   AIRG_TRY(own.alloc(&out.v, (size_t)nnz));
-  if (ar > 0) airg::note_launch(), k_spgemm_copy<<<grid_for((long long)ar * 32, 256, 152 * 64), 256, 0, s>>>(ar, ubo, g.tcol, g.tval, rp, out.ci, out.v);
+  if (ar > 0) airg::note_launch(), k_spgemm_copy<<<GRID(ar)>>>(ar, ubo, g.tcol, g.tval, rp, out.ci, out.v);
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -1046,6 +1164,10 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   const int n = A.nrows;
   L.A = A;
   L.n = n;
+  auto mark = [&](int k) {
+    if (L.ev[k]) cudaEventRecord(L.ev[k], s);
+  };
+  mark(0);
   const int m = p.poly_order + 1, mc = p.coarse_poly_order + 1;
   bool coarsest = force_coarsest || n <= p.coarse_size || n < m;
   uint8_t* strong = nullptr;
@@ -1058,6 +1180,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
     L.nf = nf;
     L.nc = n - nf;
   }
+  mark(1);
   if (coarsest) {
     L.coarsest = true;
     L.nf = 0;
@@ -1066,6 +1189,10 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
     AIRG_TRY(own.alloc(&L.alpha, mc));
     AIRG_TRY(poly_fit(A, mc, p.seed, level, L.alpha, &L.fitted, tmp, s));
     AIRG_TRY(fixed_sparsity_inverse(A, L.alpha, mc, L.Ainv, own, tmp, s));
+    mark(2);
+    mark(3);
+    mark(4);
+    mark(5);
     Ac_out = DCsr{};
     return AIRG_OK;
   }
@@ -1101,13 +1228,16 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(own.alloc(&L.Acf.ci, zcf)); AIRG_TRY(own.alloc(&L.Acf.v, zcf));
   airg::note_launch(), k_extract_fill<<<GRID(n)>>>(n, A.rp, A.ci, A.v, L.cf, fpos, L.Aff, L.Afc, L.Acf);
   KERNEL_CHECK();
+  mark(2);
   // steps 3-8
   L.m = m;
   AIRG_TRY(own.alloc(&L.alpha, m));
   AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, &L.fitted, tmp, s));
   AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s));
+  mark(3);
   // step 9
   AIRG_TRY(spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false, L.Z, own, tmp, s));
+  mark(4);
   // step 10
   AIRG_TRY(own.alloc(&L.w, nf));
   airg::note_launch(), k_one_point<<<GRID(n)>>>(n, A.rp, A.ci, A.v, strong, L.cf, fpos, L.w);
@@ -1119,11 +1249,10 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(tmp.alloc(&pc, n));
   AIRG_TRY(tmp.alloc(&P.rp, (size_t)n + 1));
   airg::note_launch(), k_P_count<<<GRID(n)>>>(n, L.cf, fpos, L.w, pc);
-  long long pz = 0;
-  AIRG_TRY(scan_i32(pc, P.rp, n, tmp, s, &pz));
-  P.nnz = (int)pz;
-  AIRG_TRY(tmp.alloc(&P.ci, pz));
-  AIRG_TRY(tmp.alloc(&P.v, pz));
+  AIRG_TRY(scan_i32(pc, P.rp, n, tmp, s, nullptr));
+  P.nnz = n;  // upper bound (only P.rp delimits rows); avoids a synchronisation
+  AIRG_TRY(tmp.alloc(&P.ci, n));
+  AIRG_TRY(tmp.alloc(&P.v, n));
   airg::note_launch(), k_P_fill<<<GRID(n)>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
   KERNEL_CHECK();
   DCsr AP;
@@ -1136,6 +1265,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   if (nc > 0) airg::note_launch(), k_R_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, L.Fnat, L.Cnat, R.rp, R.ci, R.v);
   KERNEL_CHECK();
   AIRG_TRY(spgemm(R, AP, 1.0, p.drop_Ac, true, Ac_out, own, tmp, s));
+  mark(5);
   return AIRG_OK;
 }
 

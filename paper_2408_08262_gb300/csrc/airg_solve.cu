@@ -14,48 +14,73 @@ namespace airg {
 // Kernel timing (only when profiling is enabled)
 // ------------------------------------------------------------------------------------------
 static cudaEvent_t prof_event(Profiler& P) {
-  if (P.used == P.pool.size()) {
+  std::vector<cudaEvent_t>& pool = P.capturing ? P.graph_pool : P.pool;
+  size_t& used = P.capturing ? P.graph_used : P.used;
+  if (used == pool.size()) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    P.pool.push_back(e);
+    pool.push_back(e);
   }
-  return P.pool[P.used++];
+  return pool[used++];
 }
 struct ProfScope {
   Profiler& P;
   cudaStream_t s;
   int cls;
   double bytes;
+  int level;
   cudaEvent_t a = nullptr;
-  ProfScope(Profiler& P_, cudaStream_t s_, int c, double b) : P(P_), s(s_), cls(c), bytes(b) {
+  ProfScope(Profiler& P_, cudaStream_t s_, int c, double b, int lv = 0) : P(P_), s(s_), cls(c), bytes(b), level(lv) {
     if (P.on && ((P.mask >> cls) & 1u)) {
       a = prof_event(P);
-      if (a) cudaEventRecord(a, s);
+      // inside a stream capture the record must become an event node of the graph
+      if (a) cudaEventRecordWithFlags(a, s, P.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     }
   }
   ~ProfScope() {
     if (a) {
       cudaEvent_t b = prof_event(P);
       if (b) {
-        cudaEventRecord(b, s);
-        P.pending.push_back({cls, a, b, bytes});
+        cudaEventRecordWithFlags(b, s, P.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        (P.capturing ? P.graph_recs : P.pending).push_back({cls, level, a, b, bytes});
       }
     }
   }
 };
 
+static void prof_add(Profiler& P, const Profiler::Rec& r) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+    P.launches[r.cls] += 1;
+    P.ms[r.cls] += ms;
+    P.bytes[r.cls] += r.bytes;
+    const int lv = std::min(r.level, Profiler::kMaxLv - 1);
+    P.lv_launches[lv][r.cls] += 1;
+    P.lv_ms[lv][r.cls] += ms;
+    P.lv_bytes[lv][r.cls] += r.bytes;
+  }
+  cudaGetLastError();
+}
+
+// Reads the events of the last graph replay (the caller has synchronised the stream).
+int prof_graph_read(airg_hierarchy* H) {
+  Profiler& P = H->prof;
+  if (P.graph_unread > 0) {
+    for (auto& r : P.graph_recs) prof_add(P, r);
+    P.graph_unread = 0;
+  }
+  return AIRG_OK;
+}
+
 int prof_flush(airg_hierarchy* H) {
   Profiler& P = H->prof;
+  if (P.graph_unread > 0) {
+    CU_TRY(cudaStreamSynchronize(H->s));
+    prof_graph_read(H);
+  }
   if (P.pending.empty()) return AIRG_OK;
   CU_TRY(cudaStreamSynchronize(H->s));
-  for (auto& r : P.pending) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-      P.launches[r.cls] += 1;
-      P.ms[r.cls] += ms;
-      P.bytes[r.cls] += r.bytes;
-    }
-  }
+  for (auto& r : P.pending) prof_add(P, r);
   P.pending.clear();
   P.used = 0;
   return AIRG_OK;
@@ -99,7 +124,7 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
     const SolveLevel& S = H->lv[l];
     const double* bl = bptr(l);
     double* bn = H->bwork + H->lv[l + 1].off;
-    ProfScope ps(P, s, PC_RESTRICT, S.bytes_Z);
+    ProfScope ps(P, s, PC_RESTRICT, S.bytes_Z, l);
     AIRG_TRY(dev_spmv(S.Z, bl, bl + S.nf, bn, SPMV_ADDB, S.lanes_Z, s));
   }
   // coarsest level: x = Ainv b, then x += Ainv (b - A x)
@@ -108,15 +133,15 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
     const double* bl = bptr(L);
     double* xl = x0 + S.off;
     {
-      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv);
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
       AIRG_TRY(dev_spmv(S.Ainv, bl, nullptr, xl, SPMV_SET, S.lanes_Ainv, s));
     }
     for (int it = 1; it < H->p.coarse_iters; ++it) {
       {
-        ProfScope ps(P, s, PC_COARSEST, S.bytes_A);
+        ProfScope ps(P, s, PC_COARSEST, S.bytes_A, L);
         AIRG_TRY(dev_spmv(S.A, xl, bl, H->rtmp, SPMV_RESID, S.lanes_A, s));
       }
-      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv);
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
       AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
     }
   }
@@ -125,20 +150,83 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
     const SolveLevel& S = H->lv[l];
     const double* bl = bptr(l);
     double* xl = x0 + S.off;
-    {
-      ProfScope ps(P, s, PC_PROLONG, (double)S.nf * 16.0);
+    if (H->p.n_smooth_up == 0) {
+      ProfScope ps(P, s, PC_PROLONG, (double)S.nf * 16.0, l);
       dev_gather_prolong(xl, S.nf, S.w, s);
     }
     for (int sm = 0; sm < H->p.n_smooth_up; ++sm) {
       {
-        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF);
-        AIRG_TRY(dev_spmv(S.AF, xl, bl, H->rtmp, SPMV_RESID, S.lanes_AF, s));
+        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF + (sm == 0 ? 12.0 * S.nf : 0.0), l);
+        if (sm == 0) AIRG_TRY(dev_spmv_resid_prolong(S.AF, xl, S.w, bl, H->rtmp, S.lanes_AF, s));
+        else AIRG_TRY(dev_spmv(S.AF, xl, bl, H->rtmp, SPMV_RESID, S.lanes_AF, s));
       }
-      ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv);
+      ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv, l);
       AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
     }
   }
   KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// V-cycle through a CUDA graph: captured once per hierarchy (and again if the timed kernel classes
+// change) on an internal stream, replayed on the caller's stream between two device copies.
+static int ensure_vgraph(airg_hierarchy* H) {
+  Profiler& P = H->prof;
+  const unsigned mask = P.on ? P.mask : 0u;
+  if (H->vg_exec && H->vg_mask == mask) return AIRG_OK;
+  if (H->vg_exec) {
+    if (P.graph_unread) {
+      CU_TRY(cudaStreamSynchronize(H->s));
+      prof_graph_read(H);
+    }
+    cudaGraphExecDestroy(H->vg_exec);
+    H->vg_exec = nullptr;
+  }
+  if (!H->gin) {
+    AIRG_TRY(H->solve_mem.alloc(&H->gin, std::max(H->n0, 1)));
+    AIRG_TRY(H->solve_mem.alloc(&H->gout, std::max(H->n0, 1)));
+  }
+  if (!H->cap_stream) CU_TRY(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = H->s;
+  H->s = H->cap_stream;
+  P.capturing = true;
+  P.graph_recs.clear();
+  P.graph_used = 0;
+  const long long launches0 = g_launches.load();
+  cudaError_t e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = (e == cudaSuccess) ? vcycle_solve_order(H, H->gin, H->gout) : cuda_status(e);
+  // captured kernels run only when the graph is replayed: count them there
+  H->vg_kernels = g_launches.load() - launches0;
+  g_launches.fetch_sub(H->vg_kernels);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(H->cap_stream, &g) : cudaSuccess;
+  H->s = saved;
+  P.capturing = false;
+  if (rc == AIRG_OK && e2 != cudaSuccess) rc = cuda_status(e2);
+  if (rc == AIRG_OK) rc = cuda_status(cudaGraphInstantiate(&H->vg_exec, g, 0));
+  if (g) cudaGraphDestroy(g);
+  if (rc != AIRG_OK) {
+    cudaGetLastError();
+    H->vg_exec = nullptr;
+    return rc;
+  }
+  H->vg_mask = mask;
+  return AIRG_OK;
+}
+
+int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0) {
+  if (!H->use_graph) return vcycle_solve_order(H, b0, x0);
+  AIRG_TRY(ensure_vgraph(H));
+  const size_t bytes = sizeof(double) * (size_t)H->n0;
+  if (H->prof.graph_unread) {  // the previous replay's events have not been read yet
+    CU_TRY(cudaStreamSynchronize(H->s));
+    prof_graph_read(H);
+  }
+  CU_TRY(cudaMemcpyAsync(H->gin, b0, bytes, cudaMemcpyDeviceToDevice, H->s));
+  CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+  g_launches.fetch_add(H->vg_kernels);
+  if (!H->prof.graph_recs.empty()) H->prof.graph_unread = 1;
+  CU_TRY(cudaMemcpyAsync(x0, H->gout, bytes, cudaMemcpyDeviceToDevice, H->s));
   return AIRG_OK;
 }
 
@@ -148,6 +236,7 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
 static int read_scalars(airg_hierarchy* H, int count) {
   CU_TRY(cudaMemcpyAsync(H->hsc, H->dsc, sizeof(double) * count, cudaMemcpyDeviceToHost, H->s));
   CU_TRY(cudaStreamSynchronize(H->s));
+  prof_graph_read(H);
   return AIRG_OK;
 }
 
@@ -215,7 +304,7 @@ int solve_fgmres(airg_hierarchy* H, const double* b, double* x, const airg_solve
     for (; j < restart && iters < o->max_it; ++j) {
       double* vj = H->V + (size_t)j * n;
       double* zj = H->Zk + (size_t)j * n;
-      AIRG_TRY(vcycle_solve_order(H, vj, zj));
+      AIRG_TRY(vcycle_apply(H, vj, zj));
       {
         ProfScope ps(H->prof, s, PC_TOP_OP, H->bytes_A0);
         AIRG_TRY(dev_spmv(H->A0s, zj, nullptr, H->w, SPMV_SET, H->lanes_A0, s));
@@ -295,7 +384,7 @@ int solve_richardson(airg_hierarchy* H, const double* b, double* x, const airg_s
     if (!(relres == relres) || std::isinf(relres)) { status = AIRG_ERR_NAN; break; }
     if (relres <= o->rtol) break;
     if (iters >= o->max_it) { status = AIRG_NOT_CONVERGED; break; }
-    AIRG_TRY(vcycle_solve_order(H, H->r, H->Zk));
+    AIRG_TRY(vcycle_apply(H, H->r, H->Zk));
     AIRG_TRY(dev_multi_axpy(H->Zk, n, 1, H->dsc + DS_Y, H->xp, n, s));
     iters++;
   }

@@ -216,10 +216,11 @@ def solve_both(p, op, outer="fgmres", rtol=1e-12, max_it=300):
     return xo, io, xg.cpu().numpy(), ig, Hg
 
 
-@pytest.mark.parametrize("mesh", [64, 33, 128])
-def test_solution_matches_oracle(mesh):
+@pytest.mark.parametrize("mesh,degree", [(64, 2), (64, 6), (33, 6), (128, 6)])
+def test_solution_matches_oracle(mesh, degree):
+    # (64, 2) is the 24,576-DOF pure-streaming configuration with a degree-2 polynomial
     p = P.streaming_2d(mesh)
-    xo, io, xg, ig, _ = solve_both(p, O.Params())
+    xo, io, xg, ig, _ = solve_both(p, O.Params(poly_order=degree))
     assert ig["status"] == 0 and io["status"] == 0
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
     assert abs(ig["iters"] - io["iters"]) <= 1
@@ -265,6 +266,18 @@ def test_solve_is_deterministic():
     x2, i2 = Hg.solve(b, rtol=1e-10)
     assert i1 == i2
     assert torch.equal(x1, x2)
+
+
+def test_graph_and_eager_vcycles_agree_bitwise(monkeypatch):
+    p = P.blocked_sigma_2d(80)
+    b = torch.from_numpy(p.b).cuda()
+    Hg = airg.Hierarchy(*dev(p), airg.Params())
+    xg, ig = Hg.solve(b, rtol=1e-10)
+    monkeypatch.setenv("AIRG_NO_GRAPH", "1")
+    He = airg.Hierarchy(*dev(p), airg.Params())
+    xe, ie = He.solve(b, rtol=1e-10)
+    assert ig["iters"] == ie["iters"]
+    assert torch.equal(xg, xe)
 
 
 def test_host_buffer_solve_matches_device_solve():
