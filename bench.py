@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-mesh", type=int, default=320)
+    ap.add_argument("--restart", type=int, default=30)
     return ap.parse_args()
 
 
@@ -189,7 +190,10 @@ def main():
         H = airg.Hierarchy(rp, ci, v, params)
         if profile:
             H.profile()
-        x, info = H.solve(b, rtol=args.rtol)
+            torch.cuda.nvtx.range_push("airg_solve")
+        x, info = H.solve(b, rtol=args.rtol, restart=args.restart)
+        if profile:
+            torch.cuda.nvtx.range_pop()
         kt = H.kernel_times() if profile else None
         lv = H.level_info(-1)
         H.close()
@@ -217,7 +221,7 @@ def main():
         H = airg.Hierarchy(rp, ci, v, params)
         t1 = time.perf_counter()
         H.profile([dominant])
-        x, info = H.solve(b, rtol=args.rtol)
+        x, info = H.solve(b, rtol=args.rtol, restart=args.restart)
         t2 = time.perf_counter()
         kt = H.kernel_times()[dominant]
         H.close()
@@ -249,7 +253,7 @@ def main():
     for _ in range(args.steps):
         rp2, ci2, v2 = (t.to(dev, non_blocking=True) for t in (rp_h, ci_h, v_h))
         H = airg.Hierarchy(rp2, ci2, v2, params)
-        H.solve_host(b_h, x_h, rtol=args.rtol)
+        H.solve_host(b_h, x_h, rtol=args.rtol, restart=args.restart)
         H.close()
     torch.cuda.synchronize(dev)
     e_s = time.perf_counter() - e0
