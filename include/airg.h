@@ -46,7 +46,8 @@ enum {
   AIRG_ERR_NAN = -4,        /* NaN/Inf met in a norm during the solve */
   AIRG_ERR_OOM = -5,        /* device allocation failed */
   AIRG_ERR_CUDA = -6,       /* any other CUDA runtime error */
-  AIRG_ERR_UNSUPPORTED = -7 /* a product row exceeded the library's working-set limit */
+  AIRG_ERR_UNSUPPORTED = -7, /* a product row exceeded the library's working-set limit */
+  AIRG_ERR_SCRATCH = -8      /* input too large for airg_cf_split_noalloc's fixed scratch array */
 };
 
 enum { AIRG_FP64 = 0, AIRG_FP32 = 1, AIRG_BF16_VALUES = 2 };
@@ -127,6 +128,24 @@ int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t str
  * level `level` of a setup (the level index salts the PMISR weight stream).  cf_out: device, n
  * int8; 1 = F-point, 2 = C-point.  Synchronises the stream. */
 int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out, airg_stream_t stream);
+
+/* The CF splitting of airg_cf_split, computed without allocating any device memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call cudaMalloc (or any
+ * allocating routine) at the point they need the splitting -- for example a program that reserves
+ * all device memory at start-up and allocates nothing afterwards, or a latency-critical loop in
+ * which an allocation, and the synchronisation it may trigger, is not acceptable.
+ * All temporaries live in one fixed 32 MiB device array that the library reserves on every GPU it
+ * is loaded on and keeps until the process exits.  The input needs about 5 bytes per nonzero plus
+ * 34 bytes per row; larger inputs return AIRG_ERR_SCRATCH before any GPU work.  The result is
+ * identical to airg_cf_split's (same kernels, same arithmetic).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ *     that first call outside any stream capture.
+ *   - Every call shares the one array.  Calls that can overlap on the GPU (other streams, other
+ *     host threads) race on it and must be serialised by the caller.  Each call clears what it
+ *     needs; the array otherwise keeps the last call's contents.
+ *   - Synchronises the stream.  Same arguments and cf_out encoding as airg_cf_split. */
+int airg_cf_split_noalloc(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out,
+                          airg_stream_t stream);
 
 /* Frees a hierarchy and everything it owns (NULL is allowed).  Synchronises the stream the
  * hierarchy was built on. */

@@ -18,7 +18,8 @@ _lib = None
 
 AIRG_OK, AIRG_NOT_CONVERGED = 0, 1
 STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR", -3: "zero diagonal",
-          -4: "NaN", -5: "out of memory", -6: "CUDA error", -7: "unsupported"}
+          -4: "NaN", -5: "out of memory", -6: "CUDA error", -7: "unsupported",
+          -8: "input larger than the no-allocation scratch array"}
 PROFILE_CLASSES = ["smooth_resid", "smooth_update", "restrict", "top_op", "coarsest", "prolong", "gram_schmidt"]
 
 
@@ -61,6 +62,7 @@ def lib():
         L.airg_solve_host.argtypes = L.airg_solve.argtypes
         L.airg_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.airg_cf_split.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
+        L.airg_cf_split_noalloc.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
         L.airg_free.argtypes = [C.c_void_p]
         L.airg_free.restype = None
         L.airg_num_levels.argtypes = [C.c_void_p]
@@ -80,6 +82,7 @@ def lib():
 
 
 EXPORTED = ["airg_params_default", "airg_setup", "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
+            "airg_cf_split_noalloc",
             "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
             "airg_profile_enable", "airg_kernel_times", "airg_kernel_times_level", "airg_launch_count",
             "airg_status_string"]
@@ -278,6 +281,19 @@ def cf_split(rowptr, col, val, params: Params | None = None, level: int = 0, str
     _check(lib().airg_cf_split(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf.data_ptr()), _stream(stream)),
            "airg_cf_split")
     return cf
+
+
+def cf_split_noalloc(rowptr, col, val, cf_out, params: Params | None = None, level: int = 0, stream=None):
+    """airg_cf_split_noalloc: the CF splitting written into the caller's int8 CUDA tensor cf_out,
+    with no device allocation inside the library (for callers that cannot allocate at that point;
+    see include/airg.h for the capacity and the sharing rules)."""
+    A = _csr(rowptr, col, val)
+    if not (cf_out.is_cuda and cf_out.numel() == A.n):
+        raise TypeError("cf_out must be a CUDA int8 tensor with one entry per row")
+    p = params or Params()
+    _check(lib().airg_cf_split_noalloc(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf_out.data_ptr()),
+                                       _stream(stream)), "airg_cf_split_noalloc")
+    return cf_out
 
 
 def setup(rowptr, col, val, params: Params | None = None, stream=None) -> Hierarchy:

@@ -526,6 +526,7 @@ const char* airg_status_string(int status) {
     case AIRG_ERR_OOM: return "device out of memory";
     case AIRG_ERR_CUDA: return "CUDA runtime error";
     case AIRG_ERR_UNSUPPORTED: return "product row exceeds the working-set limit";
+    case AIRG_ERR_SCRATCH: return "input exceeds the fixed scratch array of airg_cf_split_noalloc";
     default: return "unknown status";
   }
 }

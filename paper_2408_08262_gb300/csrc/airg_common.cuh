@@ -47,6 +47,7 @@ struct DCsr {
 struct Arena {
   cudaStream_t s = nullptr;
   size_t chunk_min = (size_t)64 << 20;
+  bool no_grow = false;  // true: only the chunks given up front are used (no device allocation)
   struct Chunk {
     char* base;
     size_t size, used;
@@ -66,6 +67,7 @@ struct Arena {
       }
       if (c == cur && chunks[c].size - chunks[c].used < 4096) ++cur;  // nearly full: skip from now on
     }
+    if (no_grow) return AIRG_ERR_SCRATCH;
     size_t sz = bytes > chunk_min ? bytes : chunk_min;
     void* b = nullptr;
     cudaError_t e = cudaMallocAsync(&b, sz, s);
