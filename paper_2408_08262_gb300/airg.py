@@ -101,7 +101,7 @@ class Params:
     poly_order: int = 6
     coarse_poly_order: int = 12
     coarse_iters: int = 3
-    coarse_size: int = 64
+    coarse_size: int = 30000
     max_levels: int = 64
     drop_R: float = 0.01
     drop_Ac: float = 0.001

@@ -237,7 +237,7 @@ void airg_params_default(airg_params* p) {
   p->poly_order = 6;
   p->coarse_poly_order = 12;
   p->coarse_iters = 3;
-  p->coarse_size = 64;
+  p->coarse_size = 30000;
   p->max_levels = 64;
   p->drop_R = 0.01;
   p->drop_Ac = 0.001;

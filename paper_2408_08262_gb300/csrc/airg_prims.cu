@@ -297,8 +297,10 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
   double s = 0.0;
   for (int c0 = k0; c0 < k1; c0 += kSpmvChunk) {
     const int c1 = min(c0 + kSpmvChunk, k1);
+    // matrix values and columns are read once: stream them (evict-first) so that x stays in L2
+#pragma unroll 4
     for (int k = c0 + threadIdx.x; k < c1; k += kSpmvThreads) {
-      const int c = ci[k];
+      const int c = __ldcs(ci + k);
       double xv;
       if (PROLONG && c < nrows) {
         const int src = w[c];
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
       } else {
         xv = __ldg(x + c);
       }
-      prod[k - c0] = v[k] * xv;
+      prod[k - c0] = __ldcs(v + k) * xv;
     }
     __syncthreads();
     if (has) {
