@@ -285,6 +285,34 @@ def main():
                                                    "frac": fam_bytes / max(fam_ms, 1e-9) / 1e6 / peak,
                                                    "note": "every solve-phase SpMV incl. latency-bound small levels"}}
 
+    # the mixed-precision form on the same system: V-cycle in FP32 / bf16 values, FP64 outer loop
+    forms = {}
+    for name, prec in (("fp32", 1), ("bf16_values", 2)):
+        par = airg.Params(precision=prec)
+        Hw = airg.Hierarchy(rp, ci, v, par)
+        Hw.solve(b, rtol=args.rtol, restart=args.restart)
+        Hw.close()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        su, so, its = [], [], []
+        f0.record(stream)
+        for _ in range(2):
+            t0 = time.perf_counter()
+            Hf = airg.Hierarchy(rp, ci, v, par)
+            t1 = time.perf_counter()
+            xf, inf = Hf.solve(b, rtol=args.rtol, restart=args.restart)
+            t2 = time.perf_counter()
+            Hf.close()
+            su.append(1e3 * (t1 - t0))
+            so.append(1e3 * (t2 - t1))
+            its.append(inf["iters"])
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = f0.elapsed_time(f1) / 2
+        forms[name] = {"ms_per_step": round(ms, 2), "setup_ms": round(min(su), 2), "solve_ms": round(min(so), 2),
+                       "iters": max(its), "relres": inf["relres"], "dofs_per_s": p.n / (ms / 1e3),
+                       "solve_speedup_vs_fp64": round(min(solve_ms) / min(so), 3)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -310,7 +338,7 @@ def main():
                            "solve_only_dofs_per_s": p.n / (med(solve_ms) / 1e3),
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "cpu_baseline": cpu, "mixed_precision_forms": forms,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -80,7 +80,11 @@ typedef struct {
   double drop_R;            /* relative row-wise inf-norm drop on Z */
   double drop_Ac;           /* relative row-wise inf-norm drop on A_c (diagonal always kept) */
   int n_smooth_up;          /* up F-point smooths per level */
-  int precision;            /* AIRG_FP64 (others reserved) */
+  int precision;            /* AIRG_FP64; or the mixed-precision form: AIRG_FP32 (V-cycle operators and
+                               vectors in FP32, FP32 accumulation) or AIRG_BF16_VALUES (operator values
+                               stored as bf16, vectors and accumulation FP32).  Setup (coefficient fits
+                               included), the outer residual, Arnoldi and the Hessenberg least squares
+                               stay FP64 in every mode. */
   int keep_setup;           /* 1: keep natural-numbering setup operators for airg_export_level */
   uint64_t seed;            /* seeds PMISR weights and the Box-Muller right-hand sides */
 } airg_params;

@@ -40,15 +40,32 @@ int check_params(const airg_params* p) {
   if (p->poly_order < 0 || p->poly_order > 14 || p->coarse_poly_order < 0 || p->coarse_poly_order > 14) return AIRG_ERR_ARG;
   if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0 || p->coarse_size < 0) return AIRG_ERR_ARG;
   if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
-  if (p->precision != AIRG_FP64) return AIRG_ERR_ARG;
+  if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
   return AIRG_OK;
 }
 
 // Algorithmic bytes of one SpMV with the given epilogue: the CSR arrays once, x once per column
 // (every solve operator references essentially all of its columns), y written once, and b
 // (RESID/ADDB) or y (ADD) read once.
-double spmv_bytes(const DCsr& A, bool reads_extra) {
-  return 12.0 * A.nnz + 4.0 * (A.nrows + 1) + 8.0 * A.ncols + 8.0 * A.nrows * (reads_extra ? 2 : 1);
+double spmv_bytes(const DCsr& A, bool reads_extra, double vb = 8.0, double xb = 8.0) {
+  return (vb + 4.0) * A.nnz + 4.0 * (A.nrows + 1) + xb * A.ncols + xb * A.nrows * (reads_extra ? 2 : 1);
+}
+
+// Mixed precision: copies of the V-cycle operators' values in float (vt 1) or bf16 (vt 2).
+int cast_values(const DCsr& A, int vt, void** out, Arena& a, cudaStream_t s) {
+  if (vt == 1) {
+    float* p;
+    AIRG_TRY(a.alloc(&p, std::max(A.nnz, 1)));
+    dev_cast_d2f(A.v, p, A.nnz, s);
+    *out = p;
+  } else {
+    uint16_t* p;
+    AIRG_TRY(a.alloc(&p, std::max(A.nnz, 1)));
+    dev_cast_d2bf(A.v, p, A.nnz, s);
+    *out = p;
+  }
+  CU_TRY(cudaGetLastError());
+  return AIRG_OK;
 }
 
 int copy_csr(const DCsr& A, DCsr& B, Arena& a, cudaStream_t s) {
@@ -153,6 +170,18 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   }
   H->lanes_A0 = pick_lanes(avg_len(H->A0s));
   if (ev_layout1) cudaEventRecord(ev_layout1, s);
+  // mixed-precision form: low-precision copies of every V-cycle operator
+  H->vt = H->p.precision == AIRG_FP32 ? 1 : (H->p.precision == AIRG_BF16_VALUES ? 2 : 0);
+  if (H->vt)
+    for (auto& S : H->lv) {
+      AIRG_TRY(cast_values(S.Ainv, H->vt, &S.lo_Ainv, H->solve_mem, s));
+      if (S.coarsest) {
+        AIRG_TRY(cast_values(S.A, H->vt, &S.lo_A, H->solve_mem, s));
+      } else {
+        AIRG_TRY(cast_values(S.AF, H->vt, &S.lo_AF, H->solve_mem, s));
+        AIRG_TRY(cast_values(S.Z, H->vt, &S.lo_Z, H->solve_mem, s));
+      }
+    }
   // complexities (Section "Strong tolerances"; storage complexity eq. mat_store)
   double gs = 0, os = 0, st = 0;
   for (int l = 0; l < nl; ++l) {
@@ -466,12 +495,13 @@ int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t
 int airg_profile_enable(airg_hierarchy* H, int enable) {
   if (!H) return AIRG_ERR_ARG;
   if (enable && !H->bytes_A0) {
+    const double vb = H->vt == 0 ? 8.0 : (H->vt == 1 ? 4.0 : 2.0), xb = H->vt == 0 ? 8.0 : 4.0;
     for (auto& S : H->lv) {
-      if (S.coarsest) S.bytes_A = spmv_bytes(S.A, true);
-      S.bytes_Ainv = spmv_bytes(S.Ainv, true);
+      if (S.coarsest) S.bytes_A = spmv_bytes(S.A, true, vb, xb);
+      S.bytes_Ainv = spmv_bytes(S.Ainv, true, vb, xb);
       if (!S.coarsest) {
-        S.bytes_AF = spmv_bytes(S.AF, true);
-        S.bytes_Z = spmv_bytes(S.Z, true);
+        S.bytes_AF = spmv_bytes(S.AF, true, vb, xb);
+        S.bytes_Z = spmv_bytes(S.Z, true, vb, xb);
       }
     }
     H->bytes_A0 = spmv_bytes(H->A0s, false);

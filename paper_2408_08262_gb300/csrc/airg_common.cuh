@@ -150,6 +150,14 @@ int pick_lanes(double avg_row_len);
 int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
                            cudaStream_t s);
 
+// Mixed-precision V-cycle: values float (vt 1) or bf16 (vt 2), vectors/accumulation float.
+int dev_spmv_lo(const DCsr& A, const void* vals, int vt, const float* x, const float* b, float* y, int mode, int lanes,
+                const int* w, cudaStream_t s);
+void dev_cast_d2f(const double* in, float* out, long long n, cudaStream_t s);
+void dev_cast_d2bf(const double* in, void* out, long long n, cudaStream_t s);
+void dev_cast_f2d(const float* in, double* out, long long n, cudaStream_t s);
+void dev_gather_prolong_f(float* x, int nf, const int* w, cudaStream_t s);
+
 void dev_scale(const double* x, double alpha_div, double* y, int n, cudaStream_t s);  // y = x / a
 void dev_permute(const double* in, const int* pos, double* out, int n, bool inverse, cudaStream_t s);
 void dev_gather_prolong(double* x, int nf, const int* w, cudaStream_t s);  // x[f] = x[nf + w[f]]

@@ -18,6 +18,8 @@ struct SolveLevel {
   int* lay = nullptr;  // natural index of this level -> nested solve position (non-coarsest)
   DCsr A;     // coarsest level only: the level matrix
   int lanes_AF = 4, lanes_Ainv = 4, lanes_Z = 4, lanes_A = 4;
+  // mixed precision: the same operators with float or bf16 values (nullptr in FP64 mode)
+  void *lo_AF = nullptr, *lo_Ainv = nullptr, *lo_Z = nullptr, *lo_A = nullptr;
   double bytes_AF = 0, bytes_Ainv = 0, bytes_Z = 0, bytes_A = 0;  // algorithmic bytes per SpMV
 };
 
@@ -78,6 +80,9 @@ struct airg_hierarchy {
   unsigned vg_mask = 0xffffffffu;
   long long vg_kernels = 0;  // kernel nodes in the graph (counted at every replay)
   double *gin = nullptr, *gout = nullptr;
+  // mixed precision V-cycle (precision AIRG_FP32 or AIRG_BF16_VALUES): float work vectors
+  int vt = 0;  // 0 FP64, 1 float values, 2 bf16 values
+  float *gin_f = nullptr, *gout_f = nullptr, *bwork_f = nullptr, *rtmp_f = nullptr;
   // info
   double setup_ms = 0, grid_cx = 0, op_cx = 0, storage_cx = 0, layout_ms = 0;
   std::vector<std::vector<float>> phase_ms;  // per level: CF split, extraction, polynomial, Z, P + RAP

@@ -1,6 +1,8 @@
 // Primitive kernels: scans, deterministic FP64 reductions, CSR SpMV with fused epilogues,
 // Gram-Schmidt passes and small vector kernels.  All of them are bandwidth-bound; none uses tensor
 // cores (nothing here is a dense contraction).
+#include <cuda_bf16.h>
+
 #include "airg_common.cuh"
 
 namespace airg {
@@ -278,14 +280,29 @@ constexpr int kSpmvChunk = 2048;
 // LPR lanes sum each row (LPR = 1: one thread per row, summing in storage order); a CTA owns
 // kSpmvThreads / LPR consecutive rows, so operators with long rows still give many CTAs.
 // PROLONG: first F-smoothing residual with the one-point prolongation fused in (see
-// dev_spmv_resid_prolong).
-template <int LPR, int MODE, bool PROLONG>
+// dev_spmv_resid_prolong).  VT is the stored value type (double, float or bf16), XT the vector and
+// accumulation type (double for the FP64 path, float for the mixed-precision V-cycle).
+template <typename VT>
+__device__ __forceinline__ float vt_to_f(VT v) { return (float)v; }
+template <>
+__device__ __forceinline__ float vt_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT, typename XT>
+__device__ __forceinline__ XT vmul(VT a, XT x);
+template <>
+__device__ __forceinline__ double vmul<double, double>(double a, double x) { return a * x; }
+template <>
+__device__ __forceinline__ float vmul<float, float>(float a, float x) { return a * x; }
+template <>
+__device__ __forceinline__ float vmul<__nv_bfloat16, float>(__nv_bfloat16 a, float x) { return __bfloat162float(a) * x; }
+
+template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                       const double* __restrict__ v, const double* x,
-                                                       const double* b, double* y, const int* __restrict__ w,
-                                                       double* xf) {
+                                                       const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
+                                                       const int* __restrict__ w, XT* xf) {
   constexpr int RPB = kSpmvThreads / LPR;
-  __shared__ double prod[kSpmvChunk];
+  constexpr int CHUNK = kSpmvChunk * (int)(sizeof(double) / sizeof(XT));
+  __shared__ XT prod[CHUNK];
   const int r0 = blockIdx.x * RPB;
   const int r1 = min(r0 + RPB, nrows);
   const int lane = threadIdx.x % LPR;
@@ -294,21 +311,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
   const int rb = has ? rp[row] : 0;
   const int re = has ? rp[row + 1] : 0;
   const int k0 = rp[r0], k1 = rp[r1];
-  double s = 0.0;
-  for (int c0 = k0; c0 < k1; c0 += kSpmvChunk) {
-    const int c1 = min(c0 + kSpmvChunk, k1);
+  XT s = XT(0);
+  for (int c0 = k0; c0 < k1; c0 += CHUNK) {
+    const int c1 = min(c0 + CHUNK, k1);
     // matrix values and columns are read once: stream them (evict-first) so that x stays in L2
 #pragma unroll 4
     for (int k = c0 + threadIdx.x; k < c1; k += kSpmvThreads) {
       const int c = __ldcs(ci + k);
-      double xv;
+      XT xv;
       if (PROLONG && c < nrows) {
         const int src = w[c];
-        xv = src >= 0 ? x[nrows + src] : 0.0;
+        xv = src >= 0 ? x[nrows + src] : XT(0);
       } else {
         xv = __ldg(x + c);
       }
-      prod[k - c0] = __ldcs(v + k) * xv;
+      prod[k - c0] = vmul<VT, XT>(__ldcs(v + k), xv);
     }
     __syncthreads();
     if (has) {
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
   }
   if (has && lane == 0) {
-    double out;
+    XT out;
     if (MODE == SPMV_SET) out = s;
     else if (MODE == SPMV_RESID) out = b[row] - s;
     else if (MODE == SPMV_ADD) out = y[row] + s;
@@ -330,42 +347,43 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
     y[row] = out;
     if (PROLONG) {
       const int src = w[row];
-      xf[row] = src >= 0 ? x[nrows + src] : 0.0;
+      xf[row] = src >= 0 ? x[nrows + src] : XT(0);
     }
   }
 }
 
-template <int LPR>
-static void launch_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
-                        cudaStream_t s) {
-  const int grid = ceil_div(A.nrows, kSpmvThreads / LPR);
+template <typename VT, typename XT, int LPR>
+static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
+                        const int* w, XT* xf, cudaStream_t s) {
+  const int grid = ceil_div(nrows, kSpmvThreads / LPR);
   if (w) {
-    airg::note_launch(), k_spmv<LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, w, xf);
+    airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv<LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv<LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv<LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
-    default: airg::note_launch(), k_spmv<LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, x, b, y, nullptr, nullptr); break;
+    case SPMV_SET: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    default: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
   }
 }
 
-static void spmv_dispatch(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, const int* w,
-                          double* xf, cudaStream_t s) {
+template <typename VT, typename XT>
+static void spmv_dispatch(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
+                          int lanes, const int* w, XT* xf, cudaStream_t s) {
   switch (lanes) {
-    case 1: launch_spmv<1>(A, x, b, y, mode, w, xf, s); break;
-    case 2: launch_spmv<2>(A, x, b, y, mode, w, xf, s); break;
-    case 4: launch_spmv<4>(A, x, b, y, mode, w, xf, s); break;
-    case 8: launch_spmv<8>(A, x, b, y, mode, w, xf, s); break;
-    case 16: launch_spmv<16>(A, x, b, y, mode, w, xf, s); break;
-    default: launch_spmv<32>(A, x, b, y, mode, w, xf, s); break;
+    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
   }
 }
 
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
-  spmv_dispatch(A, x, b, y, mode, lanes, nullptr, nullptr, s);
+  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s);
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -374,9 +392,55 @@ int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mod
 int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
                            cudaStream_t s) {
   if (AF.nrows <= 0) return AIRG_OK;
-  spmv_dispatch(AF, x, b, y, SPMV_RESID, lanes, w, x, s);
+  spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s);
   KERNEL_CHECK();
   return AIRG_OK;
+}
+
+// Mixed-precision V-cycle SpMVs: values stored as float (vt = 1) or bf16 (vt = 2), vectors and
+// accumulation in float.
+int dev_spmv_lo(const DCsr& A, const void* vals, int vt, const float* x, const float* b, float* y, int mode, int lanes,
+                const int* w, cudaStream_t s) {
+  if (A.nrows <= 0) return AIRG_OK;
+  float* xf = w ? const_cast<float*>(x) : nullptr;
+  if (vt == 2)
+    spmv_dispatch<__nv_bfloat16, float>(A.nrows, A.rp, A.ci, (const __nv_bfloat16*)vals, x, b, y, mode, lanes, w, xf, s);
+  else
+    spmv_dispatch<float, float>(A.nrows, A.rp, A.ci, (const float*)vals, x, b, y, mode, lanes, w, xf, s);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+__global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void k_cast_d2bf(const double* __restrict__ in, __nv_bfloat16* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16_rn((float)in[i]);
+}
+__global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+void dev_cast_d2f(const double* in, float* out, long long n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_cast_d2f<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+void dev_cast_d2bf(const double* in, void* out, long long n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_cast_d2bf<<<grid_for(n, 256), 256, 0, s>>>(in, (__nv_bfloat16*)out, n);
+}
+void dev_cast_f2d(const float* in, double* out, long long n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_cast_f2d<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+__global__ void k_gather_prolong_f(float* x, int nf, const int* __restrict__ w) {
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+    int c = w[f];
+    x[f] = c >= 0 ? x[nf + c] : 0.0f;
+  }
+}
+void dev_gather_prolong_f(float* x, int nf, const int* w, cudaStream_t s) {
+  if (nf > 0) airg::note_launch(), k_gather_prolong_f<<<grid_for(nf, 256), 256, 0, s>>>(x, nf, w);
 }
 
 // Lanes per row for the tiled SpMV: one thread per row for short rows (the sequential storage-

@@ -168,6 +168,55 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
   return AIRG_OK;
 }
 
+// The same V-cycle with float vectors and float/bf16 operator values (mixed-precision form).
+static int vcycle_lo(airg_hierarchy* H, const float* b0, float* x0) {
+  cudaStream_t s = H->s;
+  Profiler& P = H->prof;
+  const int L = (int)H->lv.size() - 1;
+  const int vt = H->vt;
+  auto bptr = [&](int l) -> const float* { return l == 0 ? b0 : H->bwork_f + H->lv[l].off; };
+  for (int l = 0; l < L; ++l) {
+    const SolveLevel& S = H->lv[l];
+    const float* bl = bptr(l);
+    float* bn = H->bwork_f + H->lv[l + 1].off;
+    ProfScope ps(P, s, PC_RESTRICT, S.bytes_Z, l);
+    AIRG_TRY(dev_spmv_lo(S.Z, S.lo_Z, vt, bl, bl + S.nf, bn, SPMV_ADDB, S.lanes_Z, nullptr, s));
+  }
+  {
+    const SolveLevel& S = H->lv[L];
+    const float* bl = bptr(L);
+    float* xl = x0 + S.off;
+    {
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
+      AIRG_TRY(dev_spmv_lo(S.Ainv, S.lo_Ainv, vt, bl, nullptr, xl, SPMV_SET, S.lanes_Ainv, nullptr, s));
+    }
+    for (int it = 1; it < H->p.coarse_iters; ++it) {
+      {
+        ProfScope ps(P, s, PC_COARSEST, S.bytes_A, L);
+        AIRG_TRY(dev_spmv_lo(S.A, S.lo_A, vt, xl, bl, H->rtmp_f, SPMV_RESID, S.lanes_A, nullptr, s));
+      }
+      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
+      AIRG_TRY(dev_spmv_lo(S.Ainv, S.lo_Ainv, vt, H->rtmp_f, nullptr, xl, SPMV_ADD, S.lanes_Ainv, nullptr, s));
+    }
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const SolveLevel& S = H->lv[l];
+    const float* bl = bptr(l);
+    float* xl = x0 + S.off;
+    if (H->p.n_smooth_up == 0) dev_gather_prolong_f(xl, S.nf, S.w, s);
+    for (int sm = 0; sm < H->p.n_smooth_up; ++sm) {
+      {
+        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF, l);
+        AIRG_TRY(dev_spmv_lo(S.AF, S.lo_AF, vt, xl, bl, H->rtmp_f, SPMV_RESID, S.lanes_AF, sm == 0 ? S.w : nullptr, s));
+      }
+      ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv, l);
+      AIRG_TRY(dev_spmv_lo(S.Ainv, S.lo_Ainv, vt, H->rtmp_f, nullptr, xl, SPMV_ADD, S.lanes_Ainv, nullptr, s));
+    }
+  }
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
 // V-cycle through a CUDA graph: captured once per hierarchy (and again if the timed kernel classes
 // change) on an internal stream, replayed on the caller's stream between two device copies.
 static int ensure_vgraph(airg_hierarchy* H) {
@@ -186,6 +235,13 @@ static int ensure_vgraph(airg_hierarchy* H) {
     AIRG_TRY(H->solve_mem.alloc(&H->gin, std::max(H->n0, 1)));
     AIRG_TRY(H->solve_mem.alloc(&H->gout, std::max(H->n0, 1)));
   }
+  if (H->vt && !H->gin_f) {
+    const size_t n = (size_t)std::max(H->n0, 1);
+    AIRG_TRY(H->solve_mem.alloc(&H->gin_f, n));
+    AIRG_TRY(H->solve_mem.alloc(&H->gout_f, n));
+    AIRG_TRY(H->solve_mem.alloc(&H->bwork_f, n));
+    AIRG_TRY(H->solve_mem.alloc(&H->rtmp_f, n));
+  }
   if (!H->cap_stream) CU_TRY(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
   cudaStream_t saved = H->s;
   H->s = H->cap_stream;
@@ -194,7 +250,8 @@ static int ensure_vgraph(airg_hierarchy* H) {
   P.graph_used = 0;
   const long long launches0 = g_launches.load();
   cudaError_t e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal);
-  int rc = (e == cudaSuccess) ? vcycle_solve_order(H, H->gin, H->gout) : cuda_status(e);
+  int rc = (e == cudaSuccess) ? (H->vt ? vcycle_lo(H, H->gin_f, H->gout_f) : vcycle_solve_order(H, H->gin, H->gout))
+                               : cuda_status(e);
   // captured kernels run only when the graph is replayed: count them there
   H->vg_kernels = g_launches.load() - launches0;
   g_launches.fetch_sub(H->vg_kernels);
@@ -215,8 +272,21 @@ static int ensure_vgraph(airg_hierarchy* H) {
 }
 
 int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0) {
-  if (!H->use_graph) return vcycle_solve_order(H, b0, x0);
+  if (!H->use_graph && !H->vt) return vcycle_solve_order(H, b0, x0);
   AIRG_TRY(ensure_vgraph(H));
+  if (H->vt) {  // FP64 in, float V-cycle, FP64 out
+    if (H->prof.graph_unread) {
+      CU_TRY(cudaStreamSynchronize(H->s));
+      prof_graph_read(H);
+    }
+    dev_cast_d2f(b0, H->gin_f, H->n0, H->s);
+    CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+    g_launches.fetch_add(H->vg_kernels);
+    if (!H->prof.graph_recs.empty()) H->prof.graph_unread = 1;
+    dev_cast_f2d(H->gout_f, x0, H->n0, H->s);
+    KERNEL_CHECK();
+    return AIRG_OK;
+  }
   const size_t bytes = sizeof(double) * (size_t)H->n0;
   if (H->prof.graph_unread) {  // the previous replay's events have not been read yet
     CU_TRY(cudaStreamSynchronize(H->s));

@@ -369,3 +369,39 @@ def test_full_size_solve_reaches_tolerance(big):
     sub.sort_indices()
     Ax = sub @ xh
     assert np.all(np.abs(big.b[rows] - Ax) <= 1e-6 * np.abs(big.b).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# Mixed-precision form: V-cycle operators and vectors in FP32 (or bf16 values), FP64 outer loop
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gen", ["2d", "3d"])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_reaches_fp64_tolerance(gen, prec):
+    p = P.blocked_sigma_2d(128) if gen == "2d" else P.kuhn_3d(32)
+    b = torch.from_numpy(p.b).cuda()
+    H64 = airg.Hierarchy(*dev(p), airg.Params(coarse_size=2000))
+    x64, i64 = H64.solve(b, rtol=1e-10)
+    Hlo = airg.Hierarchy(*dev(p), airg.Params(coarse_size=2000, precision=prec))
+    xlo, ilo = Hlo.solve(b, rtol=1e-10)
+    assert ilo["status"] == 0 and ilo["relres"] <= 1e-10  # true FP64 residual
+    assert ilo["iters"] <= i64["iters"] + (2 if prec == 1 else 4)
+    x64, xlo = x64.cpu().numpy(), xlo.cpu().numpy()
+    assert np.linalg.norm(xlo - x64) / np.linalg.norm(x64) <= 1e-8
+    if gen == "3d":  # the 32^3 instance against the oracle
+        Ho = O.Hierarchy(p.rowptr, p.col, p.val, O.Params(coarse_size=2000))
+        xo, io = Ho.solve(p.b, rtol=1e-10)
+        assert np.linalg.norm(xlo - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_mixed_precision_vcycle_is_close_to_fp64_vcycle():
+    p = P.streaming_2d(64)
+    b = torch.from_numpy(np.random.default_rng(3).standard_normal(p.n)).cuda()
+    y64 = airg.Hierarchy(*dev(p), airg.Params(coarse_size=500)).vcycle(b)
+    y32 = airg.Hierarchy(*dev(p), airg.Params(coarse_size=500, precision=1)).vcycle(b)
+    ybf = airg.Hierarchy(*dev(p), airg.Params(coarse_size=500, precision=2)).vcycle(b)
+    r32 = (torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64)).item()
+    rbf = (torch.linalg.norm(ybf - y64) / torch.linalg.norm(y64)).item()
+    assert r32 < 1e-4   # single-precision rounding through the cycle
+    assert rbf < 5e-2   # bf16 values carry 8 bits of mantissa
+    assert r32 < rbf
