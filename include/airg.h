@@ -127,6 +127,22 @@ int airg_solve(airg_hierarchy* H, const double* b, double* x, const airg_solve_o
 int airg_solve_host(airg_hierarchy* H, const double* b_host, double* x_host, const airg_solve_opts* opts,
                     airg_solve_info* info, airg_stream_t stream);
 
+/* Adjoint form.  Builds the AIRG hierarchy of A^T (a separate setup: A^T has its own strong
+ * connections) for the adjoint solve A^T lambda = g.  A is transposed on the device (deterministic:
+ * rows of A^T sorted by column) and passed to airg_setup; same parameters, errors and ownership. */
+int airg_setup_transpose(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out);
+
+/* A^T in CSR into caller-owned DEVICE arrays: rowptr_out (n+1), col_out (nnz), val_out (nnz);
+ * columns sorted within each row.  Synchronises the stream. */
+int airg_transpose(const airg_csr* A, int32_t* rowptr_out, int32_t* col_out, double* val_out, airg_stream_t stream);
+
+/* Sampled dense-dense product on a sparsity pattern: out_val[k] = (scale * lam[i]) * x[col[k]] for
+ * every stored entry k = (i, col[k]) of `pattern` (its values are not read).  With lam the adjoint
+ * solution of A^T lam = dJ/dx and scale = -1 this is dJ/dA = -lam x^T restricted to A's pattern.
+ * lam, x: device, n; out_val: device, nnz.  Does not synchronise. */
+int airg_sddmm(const airg_csr* pattern, const double* lam, const double* x, double scale, double* out_val,
+               airg_stream_t stream);
+
 /* One V-cycle from a zero guess, x = M b (b, x: device, n).  For tests and diagnostics. */
 int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t stream);
 

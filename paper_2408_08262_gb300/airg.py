@@ -63,6 +63,9 @@ def lib():
         L.airg_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.airg_cf_split.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
         L.airg_cf_split_noalloc.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
+        L.airg_setup_transpose.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_transpose.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.airg_sddmm.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
         L.airg_free.argtypes = [C.c_void_p]
         L.airg_free.restype = None
         L.airg_num_levels.argtypes = [C.c_void_p]
@@ -81,7 +84,8 @@ def lib():
     return _lib
 
 
-EXPORTED = ["airg_params_default", "airg_setup", "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
+EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_transpose", "airg_transpose", "airg_sddmm",
+            "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
             "airg_cf_split_noalloc",
             "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
             "airg_profile_enable", "airg_kernel_times", "airg_kernel_times_level", "airg_launch_count",
@@ -137,13 +141,16 @@ def _csr(rowptr, col, val) -> _Csr:
 class Hierarchy:
     """An AIRG hierarchy built on the GPU (airg_setup)."""
 
-    def __init__(self, rowptr, col, val, params: Params | None = None, stream=None):
+    def __init__(self, rowptr, col, val, params: Params | None = None, stream=None, transpose: bool = False):
+        """transpose=True builds the hierarchy of A^T (airg_setup_transpose), for adjoint solves."""
         self.params = params or Params()
         self._keep = (rowptr, col, val)
         A = _csr(rowptr, col, val)
         self.n = A.n
         h = C.c_void_p()
-        _check(lib().airg_setup(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)), "airg_setup")
+        fn = lib().airg_setup_transpose if transpose else lib().airg_setup
+        _check(fn(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)),
+               "airg_setup_transpose" if transpose else "airg_setup")
         self._h = h
 
     def close(self):
@@ -294,6 +301,75 @@ def cf_split_noalloc(rowptr, col, val, cf_out, params: Params | None = None, lev
     _check(lib().airg_cf_split_noalloc(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf_out.data_ptr()),
                                        _stream(stream)), "airg_cf_split_noalloc")
     return cf_out
+
+
+def transpose(rowptr, col, val, stream=None):
+    """A^T on the device (airg_transpose); returns (rowptr, col, val) CUDA tensors."""
+    import torch
+    A = _csr(rowptr, col, val)
+    rp = torch.empty_like(rowptr)
+    ci = torch.empty_like(col)
+    v = torch.empty_like(val)
+    _check(lib().airg_transpose(C.byref(A), C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()),
+                                C.c_void_p(v.data_ptr()), _stream(stream)), "airg_transpose")
+    return rp, ci, v
+
+
+def sddmm(rowptr, col, lam, x, scale: float = 1.0, stream=None):
+    """out[k] = scale * lam[i] * x[col[k]] on the pattern (airg_sddmm)."""
+    import torch
+    A = _Csr(rowptr.numel() - 1, col.numel(), rowptr.data_ptr(), col.data_ptr(), 0)
+    out = torch.empty(col.numel(), dtype=torch.float64, device=col.device)
+    _check(lib().airg_sddmm(C.byref(A), C.c_void_p(lam.data_ptr()), C.c_void_p(x.data_ptr()), C.c_double(scale),
+                            C.c_void_p(out.data_ptr()), _stream(stream)), "airg_sddmm")
+    return out
+
+
+def _solve_fn():
+    import torch
+
+    class SolveFn(torch.autograd.Function):
+        """x = A^-1 b with AIRG-preconditioned FGMRES; differentiable in A's values and b.
+
+        backward: lambda = A^-T g by an AIRG solve with the hierarchy of A^T (airg_setup_transpose);
+        dL/db = lambda and dL/dA = -lambda x^T on A's pattern (airg_sddmm)."""
+
+        @staticmethod
+        def forward(ctx, rowptr, col, val, b, params=None, rtol=1e-12):
+            par = params or Params()
+            H = Hierarchy(rowptr, col, val, par)
+            x, info = H.solve(b.contiguous(), rtol=rtol, max_it=500)
+            H.close()
+            if info["status"] != 0:
+                raise AirgError(info["status"], "SolveFn forward")
+            ctx.save_for_backward(rowptr, col, val, x)
+            ctx.params, ctx.rtol = par, rtol
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            rowptr, col, val, x = ctx.saved_tensors
+            HT = Hierarchy(rowptr, col, val, ctx.params, transpose=True)
+            lam, info = HT.solve(gx.contiguous(), rtol=ctx.rtol, max_it=500)
+            HT.close()
+            if info["status"] != 0:
+                raise AirgError(info["status"], "SolveFn backward")
+            gval = sddmm(rowptr, col, lam, x, -1.0) if ctx.needs_input_grad[2] else None
+            gb = lam if ctx.needs_input_grad[3] else None
+            return None, None, gval, gb, None, None
+
+    return SolveFn
+
+
+_SolveFn = None
+
+
+def solve_fn():
+    """The torch.autograd.Function of the adjoint form (SolveFn.apply(rowptr, col, val, b, params, rtol))."""
+    global _SolveFn
+    if _SolveFn is None:
+        _SolveFn = _solve_fn()
+    return _SolveFn
 
 
 def setup(rowptr, col, val, params: Params | None = None, stream=None) -> Hierarchy:

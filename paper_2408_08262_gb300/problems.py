@@ -194,6 +194,47 @@ def assemble_p1_dg(xy, tris, omega, sigma_e, q_e=1.0):
     return rowptr, col, val, b, area
 
 
+def csr_positions(rowptr: np.ndarray, col: np.ndarray, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """Positions of the entries (rows[k], cols[k]) in a CSR with sorted columns (all must exist)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    lo = rowptr[rows].astype(np.int64)
+    hi = rowptr[rows + 1].astype(np.int64)
+    # vectorised binary search inside each row
+    while True:
+        active = lo < hi
+        if not active.any():
+            break
+        mid = (lo + hi) // 2
+        c = col[np.minimum(mid, len(col) - 1)]
+        go_right = active & (c < cols)
+        lo = np.where(go_right, mid + 1, lo)
+        hi = np.where(active & ~go_right, mid, hi)
+    if not np.all(col[lo] == cols):
+        raise ValueError("entry not in pattern")
+    return lo
+
+
+def sigma_q_maps(p: Problem):
+    """Element maps of a P1 DG problem for the adjoint form: the matrix values are
+    val = val0 + sum_e sigma_e * (mass coefficient at 9 positions of element e), and the load is
+    b = sum_e q_e * |K_e| / 3 on the element's 3 DOFs.  Returns (val0, mass_pos [ne,9], mass_coef
+    [ne,9], area [ne])."""
+    m = p.meta
+    if m.get("kind") != "p1dg2d":
+        raise ValueError("P1 DG problems only")
+    area, sig = m["area"], m["sigma_e"]
+    ne = area.size
+    I, J = np.meshgrid(np.arange(3), np.arange(3), indexing="ij")
+    rows = (3 * np.arange(ne)[:, None] + I.ravel()[None, :])
+    cols = (3 * np.arange(ne)[:, None] + J.ravel()[None, :])
+    pos = csr_positions(p.rowptr, p.col, rows.ravel(), cols.ravel()).reshape(ne, 9)
+    coef = area[:, None] * (1.0 + (I == J).ravel()[None, :]) / 12.0
+    val0 = p.val.copy()
+    np.subtract.at(val0, pos.ravel(), (sig[:, None] * coef).ravel())
+    return val0, pos, coef, area
+
+
 def p1_dg_2d(n: int, theta: float, sigma=0.0, q=1.0, seed: int = BASE_SEED, jitter: float = 0.2,
              sigma_blocks: tuple | None = None, sigma_uniform: tuple | None = None) -> Problem:
     """2D upwind P1 DG system on an n x n jittered triangle mesh (3 * 2 n^2 DOFs).
@@ -220,7 +261,8 @@ def p1_dg_2d(n: int, theta: float, sigma=0.0, q=1.0, seed: int = BASE_SEED, jitt
         sig = np.full(nt, float(sigma))
     omega = np.array([math.cos(theta), math.sin(theta)])
     rowptr, col, val, b, area = assemble_p1_dg(xy, tris, omega, sig, q)
-    meta = dict(kind="p1dg2d", mesh_n=n, theta=theta, seed=seed, jitter=jitter, n_tri=nt)
+    meta = dict(kind="p1dg2d", mesh_n=n, theta=theta, seed=seed, jitter=jitter, n_tri=nt, area=area,
+                sigma_e=np.asarray(sig, dtype=np.float64))
     return Problem(3 * nt, rowptr, col, val, b, meta)
 
 
