@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-mesh", type=int, default=320)
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and adjoint form measurements")
     return ap.parse_args()
 
 
@@ -313,6 +314,74 @@ def main():
                        "iters": max(its), "relres": inf["relres"], "dofs_per_s": p.n / (ms / 1e3),
                        "solve_speedup_vs_fp64": round(min(solve_ms) / min(so), 3)}
 
+    # batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle graph,
+    # against the same 64 systems solved one after another (same hierarchies)
+    batched, adjoint = None, None
+    if not args.no_forms:
+        systems = P.batched_2d(64)
+        Hs, bs = [], []
+        for q in systems:
+            Hs.append(airg.Hierarchy(*(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)), params))
+            bs.append(torch.from_numpy(q.b).to(dev))
+        Bt = airg.Batch(Hs)
+        Bt.solve(bs, rtol=args.rtol)
+        for H, bq in zip(Hs, bs):
+            H.solve(bq, rtol=args.rtol)
+        torch.cuda.synchronize(dev)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        xs, infos = Bt.solve(bs, rtol=args.rtol)
+        e1.record(stream)
+        its_seq = []
+        for H, bq in zip(Hs, bs):
+            _, ii = H.solve(bq, rtol=args.rtol)
+            its_seq.append(ii["iters"])
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        ndofs = sum(q.n for q in systems)
+        batched = {"workload": "64 P1 DG systems, n x n with n drawn from {64,128,256,512}, theta ~ U[0,2pi), "
+                               "sigma ~ U[0,5]", "systems": len(systems), "total_dofs": ndofs,
+                   "batched_solve_ms": round(tb, 2), "sequential_solve_ms": round(ts, 2),
+                   "speedup_vs_sequential": round(ts / tb, 3), "batched_dofs_per_s": ndofs / (tb / 1e3),
+                   "iters_min": min(i["iters"] for i in infos), "iters_max": max(i["iters"] for i in infos),
+                   "all_converged": all(i["status"] == 0 for i in infos),
+                   "iters_sequential_max": max(its_seq)}
+        Bt.close()
+        del Hs
+        # adjoint form: J = w . u on 256 x 256 (393,216 DOFs) with per-element sigma; forward solve
+        # and backward (A^T hierarchy + adjoint solve + SDDMM) through the autograd Function
+        qa = P.adjoint_2d(256)
+        val0, pos, coef, area = P.sigma_q_maps(qa)
+        rpa, cia = (torch.from_numpy(a).to(dev) for a in (qa.rowptr, qa.col))
+        pos_t, coef_t = torch.from_numpy(pos.ravel()).to(dev), torch.from_numpy(coef).to(dev)
+        val0_t, area_t = torch.from_numpy(val0).to(dev), torch.from_numpy(area).to(dev)
+        wq = torch.from_numpy(np.random.default_rng(240808266).standard_normal(qa.n)).to(dev)
+        Fn = airg.solve_fn()
+
+        def fwd_bwd():
+            sg = torch.from_numpy(qa.meta["sigma_e"].copy()).to(dev).requires_grad_(True)
+            qq = torch.ones(qa.meta["n_tri"], dtype=torch.float64, device=dev, requires_grad=True)
+            val = val0_t.index_add(0, pos_t, (sg[:, None] * coef_t).reshape(-1))
+            bb = torch.repeat_interleave(qq * area_t / 3.0, 3)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a2 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            xx = Fn.apply(rpa, cia, val, bb, params, args.rtol)
+            J = (wq * xx).sum()
+            a1.record(stream)
+            J.backward()
+            a2.record(stream)
+            torch.cuda.synchronize(dev)
+            return a0.elapsed_time(a1), a1.elapsed_time(a2)
+
+        fwd_bwd()
+        f_ms, b_ms = fwd_bwd()
+        adjoint = {"workload": "256x256 P1 DG (393,216 DOFs), theta 1.1, sigma_e ~ U[0,2], J = w.u",
+                   "forward_ms": round(f_ms, 2), "backward_ms": round(b_ms, 2),
+                   "backward_over_forward": round(b_ms / f_ms, 3)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -339,6 +408,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "mixed_precision_forms": forms,
+                "batched_form": batched, "adjoint_form": adjoint,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

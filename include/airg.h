@@ -66,8 +66,9 @@ typedef struct {
  * (Section "Parallel results"): strength 0.5, n_loops^max = 3, DDC fraction 10 %, drop 0.01 on Z
  * and 0.001 on the coarse matrices, 6th-order polynomials (m = 7) with first-order fixed sparsity; two up F-smooths (Section "Results"); the coarse solve uses
  * three iterations of a 12th-order fixed-sparsity polynomial (Section "Timing results"), with the
- * hierarchy truncated at 30,000 unknowns (the paper truncates at ~300k on CPU ranks; 30k is where
- * one GB300 is fastest on the 6.29M-DOF benchmark system with unchanged iteration counts). */
+ * hierarchy truncated automatically at clamp(n_top / 16, 64, 30000) unknowns (the paper truncates
+ * at ~300k on CPU ranks; 30k is where one GB300 is fastest on the 6.29M-DOF benchmark system with
+ * unchanged iteration counts, and smaller systems keep a multilevel hierarchy). */
 typedef struct {
   double strong_threshold;  /* alpha in eq. soc, in [0, 1] */
   double ddc_fraction;      /* fraction of F-points DDC converts, in [0, 1] */
@@ -75,7 +76,8 @@ typedef struct {
   int poly_order;           /* degree d of the GMRES polynomial on A_ff (m = d+1 coefficients), <= 14 */
   int coarse_poly_order;    /* degree of the coarsest-level polynomial */
   int coarse_iters;         /* iterations of the coarsest-level polynomial solve (>= 1) */
-  int coarse_size;          /* a level with n <= coarse_size is the coarsest */
+  int coarse_size;          /* a level with n <= coarse_size is the coarsest; <= 0: automatic,
+                               clamp(n_top / 16, 64, 30000) */
   int max_levels;           /* hierarchy depth cap (>= 1) */
   double drop_R;            /* relative row-wise inf-norm drop on Z */
   double drop_Ac;           /* relative row-wise inf-norm drop on A_c (diagonal always kept) */
@@ -142,6 +144,21 @@ int airg_transpose(const airg_csr* A, int32_t* rowptr_out, int32_t* col_out, dou
  * lam, x: device, n; out_val: device, nnz.  Does not synchronise. */
 int airg_sddmm(const airg_csr* pattern, const double* lam, const double* x, double scale, double* out_val,
                airg_stream_t stream);
+
+/* Batched form: many independent systems, each with its own (FP64) hierarchy, solved together.
+ * airg_batch_create concatenates, for every hierarchy depth, the level operators of all systems
+ * into grouped CSR matrices (columns relabelled to positions in one concatenated vector, rows
+ * mapped to their positions), so every V-cycle step is one launch over all systems; the batched
+ * V-cycle is captured once as a CUDA graph.  The hierarchies must outlive the batch and share
+ * coarse_iters and n_smooth_up.  airg_solve_batched runs right-preconditioned FGMRES on every system
+ * in lockstep, with per-system (segmented) reductions and per-system convergence: b[q], x[q] are
+ * device pointers of system q's size (x holds the initial guess unless opts->x0_zero), infos has
+ * nsys entries.  Returns the worst status (a negative error if any system failed). */
+typedef struct airg_batch airg_batch;
+int airg_batch_create(airg_hierarchy* const* Hs, int nsys, airg_stream_t stream, airg_batch** out);
+int airg_solve_batched(airg_batch* B, const double* const* b, double* const* x, const airg_solve_opts* opts,
+                       airg_solve_info* infos, airg_stream_t stream);
+void airg_batch_free(airg_batch* B);
 
 /* One V-cycle from a zero guess, x = M b (b, x: device, n).  For tests and diagnostics. */
 int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t stream);

@@ -66,6 +66,10 @@ def lib():
         L.airg_setup_transpose.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
         L.airg_transpose.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.airg_sddmm.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+        L.airg_batch_create.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_solve_batched.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts), C.c_void_p, C.c_void_p]
+        L.airg_batch_free.argtypes = [C.c_void_p]
+        L.airg_batch_free.restype = None
         L.airg_free.argtypes = [C.c_void_p]
         L.airg_free.restype = None
         L.airg_num_levels.argtypes = [C.c_void_p]
@@ -85,7 +89,8 @@ def lib():
 
 
 EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_transpose", "airg_transpose", "airg_sddmm",
-            "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split",
+            "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split", "airg_batch_create",
+            "airg_solve_batched", "airg_batch_free",
             "airg_cf_split_noalloc",
             "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
             "airg_profile_enable", "airg_kernel_times", "airg_kernel_times_level", "airg_launch_count",
@@ -105,7 +110,7 @@ class Params:
     poly_order: int = 6
     coarse_poly_order: int = 12
     coarse_iters: int = 3
-    coarse_size: int = 30000
+    coarse_size: int = 0
     max_levels: int = 64
     drop_R: float = 0.01
     drop_Ac: float = 0.001
@@ -301,6 +306,40 @@ def cf_split_noalloc(rowptr, col, val, cf_out, params: Params | None = None, lev
     _check(lib().airg_cf_split_noalloc(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf_out.data_ptr()),
                                        _stream(stream)), "airg_cf_split_noalloc")
     return cf_out
+
+
+class Batch:
+    """Many systems solved together (airg_batch_create / airg_solve_batched); keeps the
+    hierarchies alive."""
+
+    def __init__(self, hierarchies, stream=None):
+        self.H = list(hierarchies)
+        arr = (C.c_void_p * len(self.H))(*[h._h.value for h in self.H])
+        b = C.c_void_p()
+        _check(lib().airg_batch_create(arr, len(self.H), _stream(stream), C.byref(b)), "airg_batch_create")
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().airg_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, restart: int = 30, max_it: int = 200, rtol: float = 1e-10, stream=None):
+        import torch
+        xs = [torch.zeros_like(b) for b in bs]
+        bp = (C.c_void_p * len(bs))(*[b.data_ptr() for b in bs])
+        xp = (C.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        infos = (_Info * len(bs))()
+        opts = _Opts(0, restart, max_it, rtol, 1)
+        rc = lib().airg_solve_batched(self._b, bp, xp, C.byref(opts), infos, _stream(stream))
+        _check(rc, "airg_solve_batched", allow_not_converged=True)
+        return xs, [dict(iters=i.iters, relres=i.relres, status=i.status, levels=i.levels) for i in infos]
 
 
 def transpose(rowptr, col, val, stream=None):

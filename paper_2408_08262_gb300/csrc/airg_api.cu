@@ -38,7 +38,7 @@ int check_params(const airg_params* p) {
   if (!(p->strong_threshold >= 0.0 && p->strong_threshold <= 1.0)) return AIRG_ERR_ARG;
   if (!(p->ddc_fraction >= 0.0 && p->ddc_fraction <= 1.0)) return AIRG_ERR_ARG;
   if (p->poly_order < 0 || p->poly_order > 14 || p->coarse_poly_order < 0 || p->coarse_poly_order > 14) return AIRG_ERR_ARG;
-  if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0 || p->coarse_size < 0) return AIRG_ERR_ARG;
+  if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0) return AIRG_ERR_ARG;
   if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
   if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
   return AIRG_OK;
@@ -80,7 +80,8 @@ double avg_len(const DCsr& A) { return A.nrows > 0 ? (double)A.nnz / A.nrows : 1
 
 int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   cudaStream_t s = H->s;
-  const SetupParams sp = to_setup(H->p);
+  SetupParams sp = to_setup(H->p);
+  if (sp.coarse_size <= 0) sp.coarse_size = (int)std::min<long long>(30000, std::max<long long>(64, (long long)Ain->n / 16));
   Arena tmp;
   tmp.s = s;
   struct Rel {
@@ -266,7 +267,7 @@ void airg_params_default(airg_params* p) {
   p->poly_order = 6;
   p->coarse_poly_order = 12;
   p->coarse_iters = 3;
-  p->coarse_size = 30000;
+  p->coarse_size = 0;
   p->max_levels = 64;
   p->drop_R = 0.01;
   p->drop_Ac = 0.001;

@@ -1,0 +1,60 @@
+"""Batched form: systems of uneven size solved together with grouped kernels and one V-cycle graph,
+against the same systems solved one by one and against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2408_08262_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2408_08262_gb300 import airg  # noqa: E402
+
+
+def dev(p):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p.rowptr, p.col, p.val))
+
+
+def systems():
+    spec = [(16, 0.3, 0.0), (24, 2.0, 1.5), (32, 4.0, 0.5), (20, 5.5, 3.0), (40, 1.0, 0.0), (12, 3.0, 4.9)]
+    return [P.p1_dg_2d(m, th, sigma=sg, seed=1000 + k) for k, (m, th, sg) in enumerate(spec)]
+
+
+def test_batched_matches_individual_solves_and_oracle():
+    ps = systems()
+    par = airg.Params(coarse_size=64)
+    Hs = [airg.Hierarchy(*dev(p), par) for p in ps]
+    assert len({H.num_levels for H in Hs}) > 1  # uneven depths
+    bs = [torch.from_numpy(p.b).cuda() for p in ps]
+    B = airg.Batch(Hs)
+    xs, infos = B.solve(bs, rtol=1e-12)
+    for p, H, b, x, info in zip(ps, Hs, bs, xs, infos):
+        xi, ii = H.solve(b, rtol=1e-12)
+        assert info["status"] == 0 and info["relres"] <= 1e-12
+        assert abs(info["iters"] - ii["iters"]) <= 1
+        assert (torch.linalg.norm(x - xi) / torch.linalg.norm(xi)).item() <= 1e-10
+    Ho = O.Hierarchy(ps[2].rowptr, ps[2].col, ps[2].val, O.Params(coarse_size=64))
+    xo, io = Ho.solve(ps[2].b, rtol=1e-12)
+    assert np.linalg.norm(xs[2].cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-10
+    B.close()
+
+
+def test_batched_restarts_and_per_system_status():
+    ps = systems()[:4]
+    Hs = [airg.Hierarchy(*dev(p), airg.Params(coarse_size=64)) for p in ps]
+    bs = [torch.from_numpy(p.b).cuda() for p in ps]
+    B = airg.Batch(Hs)
+    xs, infos = B.solve(bs, rtol=1e-12, restart=3, max_it=200)  # several restart cycles
+    for p, x, info in zip(ps, xs, infos):
+        assert info["status"] == 0
+        r = p.b - p.scipy() @ x.cpu().numpy()
+        assert np.linalg.norm(r) / np.linalg.norm(p.b) <= 1e-12
+    xs, infos = B.solve(bs, rtol=1e-30, max_it=4)
+    assert all(i["status"] == 1 and i["iters"] == 4 for i in infos)
+    zero = [torch.zeros_like(b) for b in bs]
+    xs, infos = B.solve(zero, rtol=1e-10)
+    assert all(i["iters"] == 0 for i in infos) and all(torch.count_nonzero(x) == 0 for x in xs)
