@@ -212,6 +212,8 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     if (ev_layout0 && ev_layout1 && cudaEventElapsedTime(&ms, ev_layout0, ev_layout1) == cudaSuccess) H->layout_ms = ms;
     cudaGetLastError();
   }
+  for (auto& L : H->lb)
+    if (L.fitted_dev) CU_TRY(cudaMemcpy(&L.fitted, L.fitted_dev, sizeof(int), cudaMemcpyDeviceToHost));
   H->alphas.resize(nl);
   for (int l = 0; l < nl; ++l) {
     H->alphas[l].assign(H->lb[l].m, 0.0);
@@ -227,6 +229,7 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
       L.Z.rp = L.Z.ci = nullptr; L.Ainv.rp = L.Ainv.ci = nullptr;
       L.Aff.v = L.Afc.v = L.Acf.v = L.Z.v = L.Ainv.v = nullptr;
       L.alpha = nullptr;
+      L.fitted_dev = nullptr;
     }
     H->kept = false;
   } else {

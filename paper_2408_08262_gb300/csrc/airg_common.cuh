@@ -178,7 +178,7 @@ int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t
              Arena& tmp, cudaStream_t s);
 
 // GMRES polynomial coefficients of A (m coefficients) from the Box-Muller rhs of (seed, level).
-// alpha: device m doubles; fitted: host.
+// alpha: device m doubles; fitted: device int (number of coefficients fitted before a breakdown).
 int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int* fitted, Arena& tmp,
              cudaStream_t s);
 
@@ -188,6 +188,20 @@ int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out,
 
 // C = scale * (A B) with the relative row-wise inf-norm drop (|c| < tol max|c_i.| dropped; the
 // diagonal kept when keep_diag).
+// Sparse product in padded form: row i's cnt[i] entries (sorted columns) at tcol/tval + ubo[i].
+struct SpgPadded {
+  int nrows = 0, ncols = 0;
+  long long total = 0;       // candidate slots
+  long long* ubo = nullptr;  // nrows + 1 slot offsets
+  int* beg = nullptr;        // the offsets as int (nullptr when total exceeds int range)
+  int* cnt = nullptr;
+  int* tcol = nullptr;
+  double* tval = nullptr;
+  int* err = nullptr;        // device flag: a row exceeded the block path's capacity
+};
+int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double scale, double tol, bool keep_diag,
+                  SpgPadded& out, Arena& tmp, cudaStream_t s);
+int spgemm_compact(const SpgPadded& P, DCsr& out, Arena& own, Arena& tmp, cudaStream_t s);
 int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_diag, DCsr& out, Arena& own,
            Arena& tmp, cudaStream_t s);
 
@@ -203,6 +217,7 @@ struct LevelBuild {
   int* w = nullptr;     // F index -> C index (natural C numbering), -1 none
   double* alpha = nullptr;
   int m = 0, fitted = 0;
+  int* fitted_dev = nullptr;  // device copy of `fitted`, read back once the hierarchy is built
   bool coarsest = false;
   // phase boundaries (CUDA events, recorded when non-null): start, CF split, extraction,
   // polynomial (steps 3-8), restrictor, prolongator + coarse matrix

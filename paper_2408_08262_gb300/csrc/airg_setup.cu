@@ -80,18 +80,24 @@ int validate_csr(const DCsr& A, Arena& tmp, cudaStream_t s) {
 // a_ij != 0 and |a_ij| >= alpha * max_{k != i} |a_ik|; a row with zero off-diagonal maximum has
 // no strong entry.  nS[i] = |S_i|.
 // ------------------------------------------------------------------------------------------
+// The bit pattern of a non-negative double, read as a signed 64-bit integer, orders exactly like the
+// value; comparisons of magnitudes therefore run on the integer pipe (FP64 issue is scarce on
+// sm_103a) with results identical to the FP64 comparisons.
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+
 __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
                            double alpha, uint8_t* __restrict__ strong, int* __restrict__ nS) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int b = rp[i], e = rp[i + 1];
-    double mx = 0.0;
+    long long mx = 0;
     for (int k = b; k < e; ++k)
-      if (ci[k] != i) mx = fmax(mx, fabs(v[k]));
-    const double thr = alpha * mx;
+      if (ci[k] != i) mx = max(mx, abs_bits(v[k]));
+    // alpha * max in FP64 (one multiply per row), then |a_ij| >= threshold on the bit patterns
+    const long long thr = abs_bits(alpha * __longlong_as_double(mx));
     int cnt = 0;
     for (int k = b; k < e; ++k) {
-      const double a = v[k];
-      const bool st = (mx != 0.0) && (ci[k] != i) && (a != 0.0) && (fabs(a) >= thr);
+      const long long a = abs_bits(v[k]);
+      const bool st = (mx != 0) && (ci[k] != i) && (a != 0) && (a >= thr);
       strong[k] = st;
       cnt += st;
     }
@@ -134,7 +140,8 @@ __global__ void k_pmisr_init(int n, const int* __restrict__ nS, const int* __res
   }
 }
 
-__device__ __forceinline__ bool pmisr_less(double wi, int i, double wj, int j) {
+// (w_i, i) < (w_j, j); weights are non-negative, so their bit patterns compare as integers
+__device__ __forceinline__ bool pmisr_less(long long wi, int i, long long wj, int j) {
   return wi < wj || (wi == wj && i < j);
 }
 
@@ -146,16 +153,16 @@ __global__ void k_pmisr_select(int n, const int* __restrict__ rp, const int* __r
     const int i = (int)ii;
     uint8_t isD = 0;
     if (cf[i] == 0) {
-      const double wi = w[i];
+      const long long wi = __double_as_longlong(w[i]);
       bool mn = true;
       for (int k = rp[i]; k < rp[i + 1] && mn; ++k) {
         if (!strong[k]) continue;
         const int j = ci[k];
-        if (cf[j] == 0 && !pmisr_less(wi, i, w[j], j)) mn = false;
+        if (cf[j] == 0 && !pmisr_less(wi, i, __double_as_longlong(w[j]), j)) mn = false;
       }
       for (int k = rpT[i]; k < rpT[i + 1] && mn; ++k) {
         const int j = colT[k];
-        if (cf[j] == 0 && !pmisr_less(wi, i, w[j], j)) mn = false;
+        if (cf[j] == 0 && !pmisr_less(wi, i, __double_as_longlong(w[j]), j)) mn = false;
       }
       isD = mn;
     }
@@ -220,11 +227,25 @@ __global__ void k_ddc_theta(int n, const int* __restrict__ rp, const int* __rest
 struct RadixState {
   unsigned long long prefix, mask;
   long long krem;
+  long long k;  // number of candidates to convert (0: DDC converts nothing)
 };
+
+// k = floor(fraction |F|) capped by the number of candidates (ctr[0] = |F|, ctr[1] = candidates)
+__global__ void k_ddc_init(const int* __restrict__ ctr, double fraction, RadixState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long k = (long long)floor(fraction * (double)ctr[0]);
+    if (k > ctr[1]) k = ctr[1];
+    st->prefix = 0ULL;
+    st->mask = 0ULL;
+    st->krem = k;
+    st->k = k;
+  }
+}
 
 __global__ void k_radix_hist(int n, const int8_t* __restrict__ cf, const double* __restrict__ theta,
                              const RadixState* st, int shift, unsigned* hist) {
   __shared__ unsigned sh[256];
+  if (st->k <= 0) return;
   for (int t = threadIdx.x; t < 256; t += blockDim.x) sh[t] = 0;
   __syncthreads();
   const unsigned long long prefix = st->prefix, mask = st->mask;
@@ -240,6 +261,8 @@ __global__ void k_radix_hist(int n, const int8_t* __restrict__ cf, const double*
 }
 
 __global__ void k_radix_pick(RadixState* st, int shift, unsigned* hist) {
+  if (st->k <= 0) return;
+  __syncthreads();
   if (threadIdx.x == 0) {
     long long cum = 0;
     int d = 0;
@@ -258,11 +281,12 @@ __global__ void k_radix_pick(RadixState* st, int shift, unsigned* hist) {
 
 __global__ void k_ddc_apply(int n, int8_t* __restrict__ cf, const double* __restrict__ theta, const RadixState* st,
                             int* converted) {
-  const double tau = __longlong_as_double((long long)st->prefix);
+  if (st->k <= 0) return;
+  const long long tau = (long long)st->prefix;  // bits of the selected (positive) theta
   int cnt = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double th = theta[i];
-    if (cf[i] == kF && th != 0.0 && th >= tau) { cf[i] = kC; cnt++; }
+    const long long th = __double_as_longlong(theta[i]);  // theta >= 0
+    if (cf[i] == kF && th != 0 && th >= tau) { cf[i] = kC; cnt++; }
   }
   if (cnt) atomicAdd(converted, cnt);
 }
@@ -285,9 +309,9 @@ int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t
   airg::note_launch(), k_strength<<<GRID(n)>>>(n, A.rp, A.ci, A.v, p.strong_threshold, strong, nS);
   airg::note_launch(), k_strong_T_count<<<GRID(n)>>>(n, A.rp, A.ci, strong, nST);
   KERNEL_CHECK();
-  long long nT = 0;
-  AIRG_TRY(scan_i32(nST, rpT, n, tmp, s, &nT));
-  AIRG_TRY(tmp.alloc(&colT, (size_t)nT));
+  // S^T has as many entries as S, at most nnz(A): no need to read the count back
+  AIRG_TRY(scan_i32(nST, rpT, n, tmp, s, nullptr));
+  AIRG_TRY(tmp.alloc(&colT, (size_t)std::max(A.nnz, 1)));
   airg::note_launch(), k_strong_T_fill<<<GRID(n)>>>(n, A.rp, A.ci, strong, rpT, cursor, colT);
   double* w;
   uint8_t* D;
@@ -315,31 +339,25 @@ int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t
   CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * 4, s));
   airg::note_launch(), k_ddc_theta<<<GRID(n)>>>(n, A.rp, A.ci, A.v, cf, theta, ctr);
   KERNEL_CHECK();
-  int hc[2];
-  CU_TRY(cudaMemcpyAsync(hc, ctr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CU_TRY(cudaStreamSynchronize(s));
-  const long long nF = hc[0], ncand = hc[1];
-  long long k = (long long)std::floor(p.ddc_fraction * (double)nF);
-  k = std::min(k, ncand);
-  int converted = 0;
-  if (k > 0) {
-    RadixState* st;
-    unsigned* hist;
-    AIRG_TRY(tmp.alloc(&st, 1));
-    AIRG_TRY(tmp.alloc(&hist, 256));
-    RadixState h0{0ULL, 0ULL, k};
-    CU_TRY(cudaMemcpyAsync(st, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
-    CU_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), s));
-    for (int pass = 0; pass < 8; ++pass) {
-      const int shift = 56 - 8 * pass;
-      airg::note_launch(), k_radix_hist<<<GRID(n)>>>(n, cf, theta, st, shift, hist);
-      airg::note_launch(), k_radix_pick<<<1, 256, 0, s>>>(st, shift, hist);
-    }
-    airg::note_launch(), k_ddc_apply<<<GRID(n)>>>(n, cf, theta, st, ctr + 2);
-    KERNEL_CHECK();
-    CU_TRY(cudaMemcpyAsync(&converted, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU_TRY(cudaStreamSynchronize(s));
+  // tau by radix select, all on the device (k = 0 leaves every F-point in place)
+  RadixState* st;
+  unsigned* hist;
+  AIRG_TRY(tmp.alloc(&st, 1));
+  AIRG_TRY(tmp.alloc(&hist, 256));
+  CU_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), s));
+  airg::note_launch(), k_ddc_init<<<1, 32, 0, s>>>(ctr, p.ddc_fraction, st);
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    airg::note_launch(), k_radix_hist<<<GRID(n)>>>(n, cf, theta, st, shift, hist);
+    airg::note_launch(), k_radix_pick<<<1, 256, 0, s>>>(st, shift, hist);
   }
+  airg::note_launch(), k_ddc_apply<<<GRID(n)>>>(n, cf, theta, st, ctr + 2);
+  KERNEL_CHECK();
+  int hc[3];
+  CU_TRY(cudaMemcpyAsync(hc, ctr, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  const long long nF = hc[0];
+  const int converted = hc[2];
   *nf_out = (int)(nF - converted);
   return AIRG_OK;
 }
@@ -412,99 +430,101 @@ __global__ void k_box_muller(int n, uint64_t key, double* __restrict__ z) {
   }
 }
 
-// Householder QR of a tall block held in shared memory (column-major [nc][kQrRows]).  Rows of
-// block b are [b*rows_per_block, ...) of the input, element (r, c) at in[r*rs + c*cs].  The
-// upper-triangular nc x nc factor (row-major, zeros below the diagonal and in rows past the
-// block's row count) goes to out + b*nc*nc.  Used for the first TSQR stage (the power basis) and
-// for every combine stage (stacked R factors).
-constexpr int kQrRows = 512;
+// TSQR of the tall power basis and the least-squares fit (setup steps 4-6), in one launch.
+//
+// One warp factors a tile of 32*RPL rows x C columns held entirely in registers (lane l owns rows
+// l, l+32, ...) by C Householder reflections, leaving the C x C upper-triangular factor in row k of
+// lane k.  Stage 0 tiles the basis; each later stage stacks G = 32*RPLC/C factors of the previous
+// stage and factors them again.  The warp that completes a group (the last of its G producers to
+// arrive, counted with an atomic after a fence) combines it, so the whole tree runs in the one
+// launch with no waiting; the warp that produces the single final factor also solves the small
+// least-squares problem.  The combination order is fixed by the tile numbering, so the result does
+// not depend on which warp arrives last.  Rows past n and columns past ncols are zero (appended
+// zero columns leave the leading ncols x ncols block of R unchanged, so bases of up to 4, 8 or 16
+// columns share the C = 4, 8, 16 instances).
+//
+// FP64 issue, not bandwidth, bounds this kernel on sm_103a (one warp-wide FP64 instruction per
+// about 64 clocks per SM sub-partition), so each reflection takes one warp reduction of all C dots
+// by recursive halving (about C+1 additions per lane instead of 5 per dot): the dots x.M_j of the
+// column x = M(k:, k) with the columns j >= k (j = k gives ||x||^2); with v = x - a e_k,
+// v.M_j = x.M_j - a M(k, j) and ||v||^2 = 2 |a| (|a| + |x_k|).
 constexpr int kQrMaxCols = 16;
 
-// M is the block's tile in dynamic shared memory, column-major with leading dimension kQrRows
-// (nc * kQrRows doubles).
-__global__ void __launch_bounds__(256) k_householder(const double* __restrict__ in, long long rs, long long cs,
-                                                     long long nrows, int nc, int rows_per_block,
-                                                     double* __restrict__ out) {
-  extern __shared__ double Msh[];
-  auto M = reinterpret_cast<double(*)[kQrRows]>(Msh);
-  __shared__ double red[8][kQrMaxCols + 1];
-  __shared__ double tot[kQrMaxCols + 1];
-  const long long r0 = (long long)blockIdx.x * rows_per_block;
-  const long long rem = nrows - r0;
-  const int rows = (int)(rem < rows_per_block ? rem : rows_per_block);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c = 0; c < nc; ++c)
-    for (int r = threadIdx.x; r < kQrRows; r += blockDim.x)
-      M[c][r] = (r < rows) ? in[(r0 + r) * rs + (long long)c * cs] : 0.0;
-  __syncthreads();
-  const int kmax = rows < nc ? rows : nc;
-  for (int k = 0; k < kmax; ++k) {
-    // ||x||^2 of column k, rows k..rows-1
-    double p = 0.0;
-    for (int r = k + threadIdx.x; r < rows; r += blockDim.x) p += M[k][r] * M[k][r];
-    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-    if (lane == 0) red[wid][0] = p;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][0];
-      tot[0] = t;
-    }
-    __syncthreads();
-    const double xn = sqrt(tot[0]);
-    const double x0 = M[k][k];
-    const double a = (x0 >= 0.0) ? -xn : xn;
-    __syncthreads();
-    if (threadIdx.x == 0) M[k][k] = x0 - a;  // v = x - a e1 stored in column k
-    __syncthreads();
-    // dots v . M[:, j] for j = k..nc-1 (j = k gives ||v||^2)
-    double d[kQrMaxCols];
+// Sum over the 32 lanes of p[0..N) (N = 4, 8 or 16), returned to every lane in p.
+template <int N>
+__device__ __forceinline__ void warp_sum_vec(double (&p)[N], int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  // recursive halving: after the levels xor 16, 8, ... each lane holds one partial sum
+  double q[N];
 #pragma unroll
-    for (int j = 0; j < kQrMaxCols; ++j) d[j] = 0.0;
-    for (int r = k + threadIdx.x; r < rows; r += blockDim.x) {
-      const double vr = M[k][r];
+  for (int j = 0; j < N; ++j) q[j] = p[j];
+  int width = N;
 #pragma unroll
-      for (int j = 0; j < kQrMaxCols; ++j)
-        if (j >= k && j < nc) d[j] += vr * M[j][r];
-    }
+  for (int bit = 4; bit >= 0 && width > 1; --bit) {
+    const bool upper = (lane >> bit) & 1;
+    const int h = width >> 1;
 #pragma unroll
-    for (int j = 0; j < kQrMaxCols; ++j) {
-      if (j >= k && j < nc) {
-        double t = d[j];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[wid][j] = t;
+    for (int j = 0; j < N / 2; ++j) {
+      if (j < h) {
+        const double keep = upper ? q[j + h] : q[j];
+        const double send = upper ? q[j] : q[j + h];
+        q[j] = keep + __shfl_xor_sync(FULL, send, 1 << bit);
       }
     }
-    __syncthreads();
-    for (int j = k + threadIdx.x; j < nc; j += blockDim.x) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q][j];
-      tot[j] = t;
-    }
-    __syncthreads();
-    const double vn2 = tot[k];
-    if (vn2 > 0.0) {
-      for (int j = k + 1; j < nc; ++j) {
-        const double sj = 2.0 * tot[j] / vn2;
-        for (int r = k + threadIdx.x; r < rows; r += blockDim.x) M[j][r] -= sj * M[k][r];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) M[k][k] = a;  // R(k,k); rows below k in column k are discarded
-    __syncthreads();
+    width = h;
   }
-  double* o = out + (size_t)blockIdx.x * nc * nc;
-  for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
-    const int r = t / nc, c = t % nc;
-    o[t] = (r <= c && r < kmax) ? M[c][r] : 0.0;
+  // remaining levels on the single value
+  constexpr int LG = (N == 4) ? 2 : (N == 8 ? 3 : 4);
+#pragma unroll
+  for (int bit = 4 - LG; bit >= 0; --bit) q[0] += __shfl_xor_sync(FULL, q[0], 1 << bit);
+  // lane l now holds the total of index (l >> (5 - LG)); gather all of them
+#pragma unroll
+  for (int j = 0; j < N; ++j) p[j] = __shfl_sync(FULL, q[0], j << (5 - LG));
+}
+
+template <int C, int RPL>
+__device__ __forceinline__ void house_warp(double (&M)[RPL][C], int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    double p[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) p[j] = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      if (q > 0 || lane >= k) {
+        const double x = M[q][k];
+#pragma unroll
+        for (int j = k; j < C; ++j) p[j] = fma(x, M[q][j], p[j]);
+      }
+    }
+    warp_sum_vec<C>(p, lane);
+    const double x0 = __shfl_sync(FULL, M[0][k], k);
+    const double xn = sqrt(p[k]);
+    const double a = (x0 >= 0.0) ? -xn : xn;
+    const double vn2 = 2.0 * xn * (xn + fabs(x0));
+    if (vn2 > 0.0) {
+      const double two_over = 2.0 / vn2;
+#pragma unroll
+      for (int j = k + 1; j < C; ++j) {
+        const double mkj = __shfl_sync(FULL, M[0][j], k);
+        const double f = (p[j] - a * mkj) * two_over;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          if (q > 0 || lane > k) M[q][j] = fma(-f, M[q][k], M[q][j]);
+          else if (lane == k) M[q][j] = fma(-f, x0 - a, M[q][j]);
+        }
+      }
+    }
+    if (lane == k) M[0][k] = a;
   }
 }
 
 // Least squares min || beta e1 - R(:, 2:end) y || (setup step 6), breakdown truncation when
-// |R_cc| <= 1e-12 ||R(:,c)||, Givens rotations and back substitution.  One thread.
-__global__ void k_poly_lsq(const double* __restrict__ R, int m, double* __restrict__ alpha, int* fitted) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int nc = m + 1;
+// |R_cc| <= 1e-12 ||R(:,c)||, Givens rotations and back substitution.  One thread.  R is row-major
+// with leading dimension ld >= m + 1.
+__device__ void poly_lsq(const double* R, int ld, int m, double* __restrict__ alpha, int* fitted) {
+  const int nc = ld;
   int mf = m;
   for (int c = 1; c <= m; ++c) {
     double cn = 0.0;
@@ -542,13 +562,121 @@ __global__ void k_poly_lsq(const double* __restrict__ R, int m, double* __restri
   *fitted = mf;
 }
 
+constexpr int kTsqrMaxStages = 16;
+struct TsqrPlan {
+  int nstages;                       // stage 0 tiles the basis
+  long long ntiles[kTsqrMaxStages];  // tiles (= factors produced) per stage
+  long long foff[kTsqrMaxStages];    // offset of the stage's factors in the factor buffer (doubles)
+  long long coff[kTsqrMaxStages];    // offset of the stage's group counters (stages >= 1)
+};
+
+template <int C, int RPL>
+__device__ __forceinline__ void store_factor(const double (&M)[RPL][C], int lane, double* o) {
+  if (lane < C) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) o[lane * C + j] = (j >= lane) ? M[0][j] : 0.0;
+  }
+}
+
+template <int C, int RPL, int RPLC>
+__global__ void __launch_bounds__(256) k_tsqr(const double* __restrict__ K, long long n, int ncols, TsqrPlan plan,
+                                              double* fbuf, unsigned* cnt, int m, double* __restrict__ alpha,
+                                              int* __restrict__ fitted) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int G = 32 * RPLC / C;  // factors per combined tile
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= plan.ntiles[0]) return;  // the whole warp leaves together
+  {
+    double M[RPL][C];
+    const long long r0 = w * (32LL * RPL);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const long long r = r0 + lane + 32 * q;
+#pragma unroll
+      for (int c = 0; c < C; ++c) M[q][c] = (r < n && c < ncols) ? K[(long long)c * n + r] : 0.0;
+    }
+    house_warp<C, RPL>(M, lane);
+    store_factor<C, RPL>(M, lane, fbuf + plan.foff[0] + w * C * C);
+  }
+  long long t = w;
+  for (int s = 1; s < plan.nstages; ++s) {
+    __threadfence();
+    __syncwarp();
+    const long long g = t / G, first = g * G;
+    const long long left = plan.ntiles[s - 1] - first;
+    const int gs = (int)(left < G ? left : G);
+    unsigned prev = 0;
+    if (lane == 0) prev = atomicAdd(cnt + plan.coff[s] + g, 1u);
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev != (unsigned)(gs - 1)) return;  // another producer of this group combines it
+    __threadfence();
+    double M[RPLC][C];
+    const double* src = fbuf + plan.foff[s - 1] + first * C * C;  // gs stacked C x C factors, row-major
+#pragma unroll
+    for (int q = 0; q < RPLC; ++q) {
+      const int r = lane + 32 * q;
+#pragma unroll
+      for (int c = 0; c < C; ++c) M[q][c] = (r < gs * C) ? __ldcg(src + (long long)r * C + c) : 0.0;
+    }
+    house_warp<C, RPLC>(M, lane);
+    store_factor<C, RPLC>(M, lane, fbuf + plan.foff[s] + g * C * C);
+    t = g;
+  }
+  __syncwarp();
+  if (lane == 0) poly_lsq(fbuf + plan.foff[plan.nstages - 1], C, m, alpha, fitted);
+}
+
+// Column count of the register QR instance for an nc-column basis.
+int tsqr_cols(int nc) { return nc <= 4 ? 4 : (nc <= 8 ? 8 : 16); }
+
+template <int C, int RPL, int RPLC>
+int tsqr_run(const double* K, long long n, int nc, int m, double* alpha, int* fitted, Arena& tmp, cudaStream_t s) {
+  constexpr int G = 32 * RPLC / C;
+  TsqrPlan plan{};
+  long long nt = (n + 32LL * RPL - 1) / (32LL * RPL);
+  long long ftot = 0, ctot = 0;
+  int ns = 0;
+  for (;;) {
+    if (ns >= kTsqrMaxStages) return AIRG_ERR_UNSUPPORTED;
+    plan.ntiles[ns] = nt;
+    plan.foff[ns] = ftot;
+    ftot += nt * C * C;
+    plan.coff[ns] = ctot;
+    if (ns > 0) ctot += nt;
+    ++ns;
+    if (nt == 1) break;
+    nt = (nt + G - 1) / G;
+  }
+  plan.nstages = ns;
+  double* fbuf;
+  unsigned* cnt;
+  AIRG_TRY(tmp.alloc(&fbuf, (size_t)ftot));
+  AIRG_TRY(tmp.alloc(&cnt, (size_t)std::max(1LL, ctot)));
+  if (ctot > 0) CU_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)ctot, s));
+  const long long blocks = (plan.ntiles[0] + 7) / 8;
+  airg::note_launch(), k_tsqr<C, RPL, RPLC><<<(unsigned)blocks, 256, 0, s>>>(K, n, nc, plan, fbuf, cnt, m, alpha, fitted);
+  return cuda_status(cudaGetLastError());
+}
+
+// Leaf tiles of 32*RPL rows: 8 rows per lane once the basis has enough rows to give every SM
+// sub-partition a few warps, else 2 (shorter FP64 chains per warp on small levels).
+int tsqr_fit(const double* K, long long n, int nc, int m, double* alpha, int* fitted, Arena& tmp, cudaStream_t s) {
+  const bool big = n >= 152LL * 8 * 256;
+  switch (tsqr_cols(nc)) {
+    case 4: return big ? tsqr_run<4, 8, 2>(K, n, nc, m, alpha, fitted, tmp, s) : tsqr_run<4, 2, 2>(K, n, nc, m, alpha, fitted, tmp, s);
+    case 8: return big ? tsqr_run<8, 8, 2>(K, n, nc, m, alpha, fitted, tmp, s) : tsqr_run<8, 2, 2>(K, n, nc, m, alpha, fitted, tmp, s);
+    default: return big ? tsqr_run<16, 4, 2>(K, n, nc, m, alpha, fitted, tmp, s) : tsqr_run<16, 2, 2>(K, n, nc, m, alpha, fitted, tmp, s);
+  }
+}
+
 int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int* fitted, Arena& tmp,
              cudaStream_t s) {
   const int n = A.nrows, nc = m + 1;
   if (m < 1 || nc > kQrMaxCols) return AIRG_ERR_ARG;
   if (n == 0) {
     CU_TRY(cudaMemsetAsync(alpha, 0, sizeof(double) * m, s));
-    *fitted = 0;
+    CU_TRY(cudaMemsetAsync(fitted, 0, sizeof(int), s));
     return AIRG_OK;
   }
   double* K;
@@ -557,29 +685,9 @@ int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int*
   KERNEL_CHECK();
   const int lanes = pick_lanes((double)A.nnz / std::max(1, n));
   for (int c = 1; c < nc; ++c) AIRG_TRY(dev_spmv(A, K + (size_t)(c - 1) * n, nullptr, K + (size_t)c * n, SPMV_SET, lanes, s));
-  // TSQR: stage 1 on the power basis, then combine stacked factors until one remains
-  const size_t qr_smem = sizeof(double) * (size_t)nc * kQrRows;
-  if (qr_smem > 48 * 1024)
-    CU_TRY(cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr_smem));
-  long long nb = (n + kQrRows - 1) / kQrRows;
-  double* R;
-  AIRG_TRY(tmp.alloc(&R, (size_t)nb * nc * nc));
-  airg::note_launch(), k_householder<<<(int)nb, 256, qr_smem, s>>>(K, 1, n, n, nc, kQrRows, R);
-  KERNEL_CHECK();
-  const int group = std::max(1, kQrRows / nc);
-  while (nb > 1) {
-    long long nb2 = (nb + group - 1) / group;
-    double* R2;
-    AIRG_TRY(tmp.alloc(&R2, (size_t)nb2 * nc * nc));
-    airg::note_launch(), k_householder<<<(int)nb2, 256, qr_smem, s>>>(R, nc, 1, nb * nc, nc, group * nc, R2);
-    KERNEL_CHECK();
-    R = R2;
-    nb = nb2;
-  }
   int* dfit;
   AIRG_TRY(tmp.alloc(&dfit, 1));
-  airg::note_launch(), k_poly_lsq<<<1, 32, 0, s>>>(R, m, alpha, dfit);
-  KERNEL_CHECK();
+  AIRG_TRY(tsqr_fit(K, n, nc, m, alpha, dfit, tmp, s));
   CU_TRY(cudaMemcpyAsync(fitted, dfit, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU_TRY(cudaStreamSynchronize(s));
   return AIRG_OK;
@@ -618,17 +726,53 @@ __global__ void k_fs_init(int nnz, const int* __restrict__ rowidx, const int* __
   }
 }
 
-__global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
-                           const int* __restrict__ ci, const double* __restrict__ v, const double* __restrict__ prev,
-                           double* __restrict__ cur, double* __restrict__ ainv, const double* __restrict__ alpha_p) {
-  const double ap = *alpha_p;
+// For entry k = (i, j) of the pattern and each q in row i (l = ci[q]), the position of a_lj in row
+// l, or -1: the gather the paper describes as done once, after which every power reads it.
+// Row i's block of the index holds r_i x r_i entries (r_i = row length) at base[i].
+__global__ void k_fs_rowsq(int n, const int* __restrict__ rp, long long* __restrict__ sq) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = rp[i + 1] - rp[i];
+    sq[i] = r * r;
+  }
+}
+__global__ void k_fs_gather(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
+                            const int* __restrict__ ci, const long long* __restrict__ ntot, long long cap,
+                            const long long* __restrict__ base, int* __restrict__ idx) {
+  if (*ntot > cap) return;  // too large: the powers search instead
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
     const int i = rowidx[k], j = ci[k];
+    const int b = rp[i], r = rp[i + 1] - b;
+    int* o = idx + base[i] + (long long)(k - b) * r;
+    for (int q = 0; q < r; ++q) {
+      const int l = ci[b + q];
+      o[q] = find_col(ci, rp[l], rp[l + 1], j);
+    }
+  }
+}
+__global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
+                           const int* __restrict__ ci, const long long* __restrict__ ntot, long long cap,
+                           const long long* __restrict__ base, const int* __restrict__ idx,
+                           const double* __restrict__ v, const double* __restrict__ prev, double* __restrict__ cur,
+                           double* __restrict__ ainv, const double* __restrict__ alpha_p) {
+  const double ap = *alpha_p;
+  const bool gathered = *ntot <= cap;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int i = rowidx[k];
+    const int b = rp[i], r = rp[i + 1] - b;
     double acc = 0.0;
-    for (int q = rp[i]; q < rp[i + 1]; ++q) {
-      const int l = ci[q];
-      const int t = find_col(ci, rp[l], rp[l + 1], j);
-      if (t >= 0) acc = fma(prev[q], v[t], acc);
+    if (gathered) {
+      const int* g = idx + base[i] + (long long)(k - b) * r;
+      for (int q = 0; q < r; ++q) {
+        const int t = g[q];
+        if (t >= 0) acc = fma(prev[b + q], v[t], acc);
+      }
+    } else {  // rows of hundreds of entries (dense coarse levels): search every position
+      const int j = ci[k];
+      for (int q = b; q < b + r; ++q) {
+        const int l = ci[q];
+        const int t = find_col(ci, rp[l], rp[l + 1], j);
+        if (t >= 0) acc = fma(prev[q], v[t], acc);
+      }
     }
     cur[k] = acc;
     ainv[k] = fma(ap, acc, ainv[k]);
@@ -649,12 +793,25 @@ int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out,
   KERNEL_CHECK();
   if (m > 2) {
     double *pa, *pb;
+    long long *sq, *base;
+    int* idx;
     AIRG_TRY(tmp.alloc(&pa, nnz));
     AIRG_TRY(tmp.alloc(&pb, nnz));
+    AIRG_TRY(tmp.alloc(&sq, n));
+    AIRG_TRY(tmp.alloc(&base, (size_t)n + 1));
+    airg::note_launch(), k_fs_rowsq<<<GRID(n)>>>(n, A.rp, sq);
+    // the gathered index costs sum_i r_i^2 ints: it is used when that is at most 128 per nonzero
+    // (and 2 GiB), decided on the device from base[n]; otherwise every power searches
+    AIRG_TRY(scan_i64(sq, base, n, tmp, s, nullptr));
+    const long long cap = std::min(128LL * nnz, 1LL << 29);
+    AIRG_TRY(tmp.alloc(&idx, (size_t)cap));
+    airg::note_launch(), k_fs_gather<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, base + n, cap, base, idx);
+    KERNEL_CHECK();
     const double* prev = A.v;
     double* cur = pa;
     for (int p = 2; p < m; ++p) {
-      airg::note_launch(), k_fs_power<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, A.v, prev, cur, out.v, alpha + p);
+      airg::note_launch(), k_fs_power<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, base + n, cap, base, idx, A.v, prev, cur,
+                                                     out.v, alpha + p);
       KERNEL_CHECK();
       prev = cur;
       cur = (cur == pa) ? pb : pa;
@@ -674,12 +831,12 @@ constexpr int kWarpCap = 1024;
 constexpr int kBlockCapMax = 32768;
 
 __global__ void k_spgemm_ub(int ar, const int* __restrict__ arp, const int* __restrict__ aci,
-                            const int* __restrict__ brp, long long* __restrict__ ub) {
+                            const int* __restrict__ brp, const int* __restrict__ blen, long long* __restrict__ ub) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ar; i += (long long)gridDim.x * blockDim.x) {
     long long t = 0;
     for (int k = arp[i]; k < arp[i + 1]; ++k) {
       const int l = aci[k];
-      t += brp[l + 1] - brp[l];
+      t += blen ? blen[l] : brp[l + 1] - brp[l];
     }
     ub[i] = t;
   }
@@ -691,7 +848,9 @@ struct SpgArgs {
   const double* av;
   const int *brp, *bci;
   const double* bv;
+  const int *bbeg, *blen;  // B in padded form (row l at bbeg[l], blen[l] entries); nullptr: CSR brp
   double scale, tol;
+  int scale_mode;  // 0: scale == 1, 1: scale == -1 (a sign flip), 2: general
   int keep_diag;
   const long long* ubo;
   int* tcol;
@@ -745,14 +904,37 @@ __device__ int warp_unique_sorted(int* a, int P, int lane) {
   return outc;
 }
 
+// scale * x; the factors 1 and -1 are applied exactly on the integer pipe
+__device__ __forceinline__ double spg_scale(const SpgArgs& g, double x) {
+  if (g.scale_mode == 0) return x;
+  if (g.scale_mode == 1) return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+  return g.scale * x;
+}
+// bit pattern of tol * max|c| from the bit pattern of max|c|; |c| < tol * max  <=>  abs_bits(c) < result
+__device__ __forceinline__ long long spg_thr(const SpgArgs& g, long long mx_bits) {
+  return abs_bits(g.tol * __longlong_as_double(mx_bits));
+}
+
+__device__ __forceinline__ void spg_brow(const SpgArgs& g, int l, int& b, int& e) {
+  if (g.blen) {
+    b = g.bbeg[l];
+    e = b + g.blen[l];
+  } else {
+    b = g.brp[l];
+    e = g.brp[l + 1];
+  }
+}
+
 __device__ __forceinline__ double spg_value(const SpgArgs& g, int ab, int ae, int j) {
   double acc = 0.0;
   for (int k = ab; k < ae; ++k) {
     const int l = g.aci[k];
-    const int t = find_col(g.bci, g.brp[l], g.brp[l + 1], j);
+    int b0, b1;
+    spg_brow(g, l, b0, b1);
+    const int t = find_col(g.bci, b0, b1, j);
     if (t >= 0) acc = fma(g.av[k], g.bv[t], acc);
   }
-  return g.scale * acc;
+  return spg_scale(g, acc);
 }
 
 // Short rows (candidate count <= kThreadCap): one thread per row.  For each A entry in ascending
@@ -774,7 +956,9 @@ __global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows,
     for (int k = ab; k < ae; ++k) {
       const int l = g.aci[k];
       const double a = g.av[k];
-      for (int q = g.brp[l]; q < g.brp[l + 1]; ++q) {
+      int qb, qe;
+      spg_brow(g, l, qb, qe);
+      for (int q = qb; q < qe; ++q) {
         const int j = g.bci[q];
         const double bv = g.bv[q];
         int pos = u;
@@ -789,18 +973,18 @@ __global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows,
         ++u;
       }
     }
-    double mx = 0.0;
+    long long mx = 0;
     for (int t = 0; t < u; ++t) {
-      acc[t] = g.scale * acc[t];
-      mx = fmax(mx, fabs(acc[t]));
+      acc[t] = spg_scale(g, acc[t]);
+      mx = max(mx, abs_bits(acc[t]));
     }
-    const double thr = g.tol * mx;
+    const long long thr = spg_thr(g, mx);
     const long long o = g.ubo[i];
     int outc = 0;
     for (int t = 0; t < u; ++t) {
       const double c = acc[t];
       const int j = cand[t];
-      if (!(fabs(c) < thr) || (g.keep_diag && j == i)) {
+      if (abs_bits(c) >= thr || (g.keep_diag && j == i)) {
         g.tcol[o + outc] = j;
         g.tval[o + outc] = c;
         ++outc;
@@ -865,7 +1049,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
     for (int k = ab; k < ae; ++k) {
       const int l = g.aci[k];
       const double a = g.av[k];
-      const int b0 = g.brp[l], len = g.brp[l + 1] - b0;
+      int b0, b1;
+      spg_brow(g, l, b0, b1);
+      const int len = b1 - b0;
       for (int t = lane; t < len; t += 32) {
         const int j = g.bci[b0 + t];
         const double bv = g.bv[b0 + t];
@@ -896,21 +1082,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
       u += __popc(bal);
       __syncwarp();
     }
+    long long mx = 0;
+    for (int t = lane; t < u; t += 32) {
+      const double c = spg_scale(g, val[t]);
+      val[t] = c;
+      mx = max(mx, abs_bits(c));
+    }
+    for (int s2 = 16; s2 > 0; s2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
+    const long long thr = spg_thr(g, mx);
+    const long long o = g.ubo[i];
     int P = 32;
     while (P < u) P <<= 1;
     for (int t = u + lane; t < P; t += 32) { key[t] = 0x7fffffff; val[t] = 0.0; }
     __syncwarp();
     bitonic_sort_kv<32>(key, val, P, lane);
-    double mx = 0.0;
-    for (int t = lane; t < u; t += 32) {
-      const double c = g.scale * val[t];
-      val[t] = c;
-      mx = fmax(mx, fabs(c));
-    }
-    for (int s2 = 16; s2 > 0; s2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
-    const double thr = g.tol * mx;
-    __syncwarp();
-    const long long o = g.ubo[i];
     int outc = 0;
     for (int base = 0; base < u; base += 32) {
       const int t = base + lane;
@@ -920,7 +1105,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
       if (t < u) {
         j = key[t];
         c = val[t];
-        keep = !(fabs(c) < thr) || (g.keep_diag && j == i);
+        keep = abs_bits(c) >= thr || (g.keep_diag && j == i);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) {
@@ -935,13 +1120,193 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
   }
 }
 
+// Writes the kept entries of a warp's compacted row (key/val[0..u), u <= 32*NE) in column order:
+// a kept entry's position is the number of kept columns below it (dropped entries take the key
+// 0x7fffffff, which is below no kept column).  Returns the number kept.
+template <int NE>
+__device__ __forceinline__ int spg_rank_write(const SpgArgs& g, int* key, const double* val, int u, long long thr,
+                                              int i, long long o, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  int mk[NE];
+  double mv[NE];
+  int kept = 0;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int t = lane + 32 * e;
+    int j = 0x7fffffff;
+    double c = 0.0;
+    if (t < u) {
+      j = key[t];
+      c = val[t];
+      if (!(abs_bits(c) >= thr || (g.keep_diag && j == i))) j = 0x7fffffff;
+    }
+    mk[e] = j;
+    mv[e] = c;
+    kept += __popc(__ballot_sync(FULL, j != 0x7fffffff));
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+    if (lane + 32 * e < u) key[lane + 32 * e] = mk[e];
+  __syncwarp();
+  int rk[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) rk[e] = 0;
+  for (int t = 0; t < u; ++t) {
+    const int kt = key[t];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) rk[e] += (kt < mk[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+    if (mk[e] != 0x7fffffff) {
+      g.tcol[o + rk[e]] = mk[e];
+      g.tval[o + rk[e]] = mv[e];
+    }
+  return kept;
+}
+
+// Medium rows, staged: one warp per row with at most kStageCap candidates and kStageA entries in A's
+// row.  The row's A entries (value, B row start, candidate offset) and then all of its candidates
+// (column, B value) are first copied into shared memory with every load of a phase issued at once,
+// so the accumulation loop that follows (in ascending A order, as in k_spgemm_warp) touches only
+// shared memory instead of waiting on three dependent global loads per A entry.  Other rows go on
+// to `next_rows`.
+constexpr int kStageCap = 256;
+constexpr int kStageA = 64;
+constexpr int kStageWarps = 8;
+
+struct WarpStage {
+  double cb[kStageCap];
+  double hval[kStageCap];
+  double ea[kStageA];
+  int cj[kStageCap];
+  int hkey[kStageCap];
+  int epre[kStageA + 1];
+  int eb[kStageA];
+};
+
+__global__ void __launch_bounds__(kStageWarps * 32) k_spgemm_warp_staged(SpgArgs g, const int* __restrict__ rows,
+                                                                         const int* __restrict__ nrows_dev,
+                                                                         int* next_rows, int* n_next) {
+  extern __shared__ __align__(16) unsigned char stage_raw[];
+  constexpr unsigned FULL = 0xffffffffu;
+  const int nrows = *nrows_dev;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpStage& W = reinterpret_cast<WarpStage*>(stage_raw)[wid];
+  int* key = W.hkey;
+  double* val = W.hval;
+  const long long gw = (long long)blockIdx.x * kStageWarps + wid;
+  const long long nw = (long long)gridDim.x * kStageWarps;
+  for (long long ii = gw; ii < nrows; ii += nw) {
+    const int i = rows[ii];
+    const int ub = (int)(g.ubo[i + 1] - g.ubo[i]);
+    const int ab = g.arp[i], na = g.arp[i + 1] - ab;
+    if (ub > kStageCap || na > kStageA) {
+      if (lane == 0) next_rows[atomicAdd(n_next, 1)] = i;
+      continue;
+    }
+    // A entries: value, B row start, candidate offset (exclusive scan of the B row lengths)
+    int carry = 0;
+    for (int e0 = 0; e0 < na; e0 += 32) {
+      const int e = e0 + lane;
+      int len = 0;
+      if (e < na) {
+        const int l = g.aci[ab + e];
+        W.ea[e] = g.av[ab + e];
+        int b0, b1;
+        spg_brow(g, l, b0, b1);
+        W.eb[e] = b0;
+        len = b1 - b0;
+      }
+      int inc = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (e < na) W.epre[e] = carry + inc - len;
+      carry += __shfl_sync(FULL, inc, 31);
+    }
+    if (lane == 0) W.epre[na] = carry;
+    int H = 32, lg = 5;
+    while (H < ub) { H <<= 1; ++lg; }
+    for (int t = lane; t < H; t += 32) { key[t] = -1; val[t] = 0.0; }
+    __syncwarp();
+    // candidates: candidate c belongs to the last A entry whose offset is <= c
+    for (int c = lane; c < ub; c += 32) {
+      int lo = 0, hi = na - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (W.epre[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      const int q = W.eb[lo] + (c - W.epre[lo]);
+      W.cj[c] = g.bci[q];
+      W.cb[c] = g.bv[q];
+    }
+    __syncwarp();
+    // accumulate in ascending A order (one A entry at a time, its candidates across the lanes)
+    for (int e = 0; e < na; ++e) {
+      const int c1 = W.epre[e + 1];
+      const double a = W.ea[e];
+      for (int c = W.epre[e] + lane; c < c1; c += 32) {
+        const int j = W.cj[c];
+        unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - lg);
+        while (true) {
+          const int prev = atomicCAS(&key[h], -1, j);
+          if (prev == -1 || prev == j) break;
+          h = (h + 1) & (H - 1);
+        }
+        val[h] = fma(a, W.cb[c], val[h]);
+      }
+      __syncwarp();
+    }
+    // compact occupied slots to the front (chunks read before written)
+    int u = 0;
+    for (int base = 0; base < H; base += 32) {
+      const int idx = base + lane;
+      const int kk = key[idx];
+      const double vv = val[idx];
+      const bool occ = kk >= 0;
+      const unsigned bal = __ballot_sync(FULL, occ);
+      __syncwarp();
+      if (occ) {
+        const int d = u + __popc(bal & ((1u << lane) - 1u));
+        key[d] = kk;
+        val[d] = vv;
+      }
+      u += __popc(bal);
+      __syncwarp();
+    }
+    long long mx = 0;
+    for (int t = lane; t < u; t += 32) {
+      const double c = spg_scale(g, val[t]);
+      val[t] = c;
+      mx = max(mx, abs_bits(c));
+    }
+    for (int s2 = 16; s2 > 0; s2 >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, s2));
+    const long long thr = spg_thr(g, mx);
+    const long long o = g.ubo[i];
+    // order by rank: a kept entry's output position is the number of kept columns below it;
+    // dropped entries take the key 0x7fffffff, which is below no kept column
+    int kept;
+    if (u <= 32) kept = spg_rank_write<1>(g, key, val, u, thr, i, o, lane);
+    else if (u <= 64) kept = spg_rank_write<2>(g, key, val, u, thr, i, o, lane);
+    else if (u <= 128) kept = spg_rank_write<4>(g, key, val, u, thr, i, o, lane);
+    else kept = spg_rank_write<8>(g, key, val, u, thr, i, o, lane);
+    if (lane == 0) g.cnt[i] = kept;
+    __syncwarp();
+  }
+}
+
 // Long rows: one 256-thread CTA per row (grid-stride over the device-side list), dynamic shared
 // memory of `cap` ints; a row beyond `cap` candidates sets *err and is skipped.
 __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __restrict__ rows,
                                                       const int* __restrict__ nrows_dev, int cap, int* err) {
   extern __shared__ int bbuf[];
   __shared__ int wcnt[8];
-  __shared__ double wmx[8];
+  __shared__ long long wmx[8];
   const int nrows = *nrows_dev;
   for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
   const int i = rows[rr];
@@ -955,7 +1320,9 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
   int off = 0;
   for (int k = ab; k < ae; ++k) {
     const int l = g.aci[k];
-    const int b0 = g.brp[l], len = g.brp[l + 1] - b0;
+    int b0, b1;
+    spg_brow(g, l, b0, b1);
+    const int len = b1 - b0;
     for (int t = t0; t < len; t += 256) bbuf[off + t] = g.bci[b0 + t];
     off += len;
   }
@@ -985,20 +1352,20 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
     __syncthreads();
   }
   const long long o = g.ubo[i];
-  double mx = 0.0;
+  long long mx = 0;
   for (int t = t0; t < u; t += 256) {
     const int j = bbuf[t];
     const double c = spg_value(g, ab, ae, j);
     g.tcol[o + t] = j;
     g.tval[o + t] = c;
-    mx = fmax(mx, fabs(c));
+    mx = max(mx, abs_bits(c));
   }
-  for (int s2 = 16; s2 > 0; s2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
+  for (int s2 = 16; s2 > 0; s2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
   if (lane == 0) wmx[wid] = mx;
   __syncthreads();
-  mx = 0.0;
-  for (int q = 0; q < 8; ++q) mx = fmax(mx, wmx[q]);
-  const double thr = g.tol * mx;
+  mx = 0;
+  for (int q = 0; q < 8; ++q) mx = max(mx, wmx[q]);
+  const long long thr = spg_thr(g, mx);
   int outc = 0;
   for (int base = 0; base < u; base += 256) {
     const int t = base + t0;
@@ -1008,7 +1375,7 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
     if (t < u) {
       j = g.tcol[o + t];
       c = g.tval[o + t];
-      keep = !(fabs(c) < thr) || (g.keep_diag && j == i);
+      keep = abs_bits(c) >= thr || (g.keep_diag && j == i);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) wcnt[wid] = __popc(bal);
@@ -1028,35 +1395,63 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
   }
 }
 
-__global__ void k_spgemm_copy(int ar, const long long* __restrict__ ubo, const int* __restrict__ tcol,
-                              const double* __restrict__ tval, const int* __restrict__ rp, int* __restrict__ ci,
-                              double* __restrict__ v) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ar; i += (long long)gridDim.x * blockDim.x) {
-    const long long o = ubo[i];
-    const int b = rp[i], len = rp[i + 1] - b;
-    for (int t = 0; t < len; ++t) {
-      ci[b + t] = tcol[o + t];
-      v[b + t] = tval[o + t];
+// Compaction of the per-row results (at the candidate offsets ubo) into CSR: a CTA takes 256
+// consecutive rows, whose output is one contiguous range; each thread finds its entry's row by
+// binary search over the CTA's row starts in shared memory, so the writes are coalesced.
+__global__ void __launch_bounds__(256) k_spgemm_copy(int ar, const long long* __restrict__ ubo,
+                                                     const int* __restrict__ tcol, const double* __restrict__ tval,
+                                                     const int* __restrict__ rp, int* __restrict__ ci,
+                                                     double* __restrict__ v) {
+  __shared__ int srp[257];
+  __shared__ long long sub[256];
+  const int r0 = blockIdx.x * 256;
+  const int nr = min(256, ar - r0);
+  for (int t = threadIdx.x; t <= nr; t += 256) srp[t] = rp[r0 + t];
+  if (threadIdx.x < nr) sub[threadIdx.x] = ubo[r0 + threadIdx.x];
+  __syncthreads();
+  const int b = srp[0], e = srp[nr];
+  for (int p = b + threadIdx.x; p < e; p += 256) {
+    int lo = 0, hi = nr - 1;  // last row whose start is <= p
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (srp[mid] <= p) lo = mid;
+      else hi = mid - 1;
     }
+    const long long src = sub[lo] + (p - srp[lo]);
+    ci[p] = tcol[src];
+    v[p] = tval[src];
   }
 }
 
-int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_diag, DCsr& out, Arena& own,
-           Arena& tmp, cudaStream_t s) {
+__global__ void k_i64_to_i32(int n, const long long* __restrict__ in, int* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (int)in[i];
+}
+
+// Product into the padded form: row i's cnt[i] entries at tcol/tval + ubo[i] (ubo = exclusive scan
+// of the candidate counts).  B is CSR (Bc) or padded (Bp).
+int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double scale, double tol, bool keep_diag,
+                  SpgPadded& out, Arena& tmp, cudaStream_t s) {
   const int ar = A.nrows;
-  long long *ub, *ubo;
+  long long* ub;
   AIRG_TRY(tmp.alloc(&ub, std::max(ar, 1)));
-  AIRG_TRY(tmp.alloc(&ubo, (size_t)ar + 1));
-  if (ar > 0) airg::note_launch(), k_spgemm_ub<<<GRID(ar)>>>(ar, A.rp, A.ci, B.rp, ub);
+  AIRG_TRY(tmp.alloc(&out.ubo, (size_t)ar + 1));
+  if (ar > 0)
+    airg::note_launch(), k_spgemm_ub<<<GRID(ar)>>>(ar, A.rp, A.ci, Bc ? Bc->rp : nullptr, Bc ? nullptr : Bp->cnt, ub);
   KERNEL_CHECK();
   long long total = 0;
-  AIRG_TRY(scan_i64(ub, ubo, ar, tmp, s, &total));
+  AIRG_TRY(scan_i64(ub, out.ubo, ar, tmp, s, &total));
   SpgArgs g{};
   g.ar = ar;
   g.arp = A.rp; g.aci = A.ci; g.av = A.v;
-  g.brp = B.rp; g.bci = B.ci; g.bv = B.v;
+  if (Bc) {
+    g.brp = Bc->rp; g.bci = Bc->ci; g.bv = Bc->v;
+  } else {
+    g.bbeg = Bp->beg; g.blen = Bp->cnt; g.bci = Bp->tcol; g.bv = Bp->tval;
+  }
   g.scale = scale; g.tol = tol; g.keep_diag = keep_diag ? 1 : 0;
-  g.ubo = ubo;
+  g.scale_mode = (scale == 1.0) ? 0 : (scale == -1.0 ? 1 : 2);
+  g.ubo = out.ubo;
   AIRG_TRY(tmp.alloc(&g.tcol, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.tval, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.cnt, std::max(ar, 1)));
@@ -1069,7 +1464,13 @@ int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_dia
   CU_TRY(cudaMemsetAsync(ctr, 0, 4 * sizeof(int), s));
   if (ar > 0) {
     airg::note_launch(), k_spgemm_thread<<<grid_for(ar, 128, 152 * 64), 128, 0, s>>>(g, mid, ctr + 0);
-    airg::note_launch(), k_spgemm_warp<256, 16><<<152 * 4, 16 * 32, 0, s>>>(g, mid, ctr + 0, big, ctr + 1);
+    static bool stage_set = false;
+    const size_t stage_smem = sizeof(WarpStage) * kStageWarps;
+    if (!stage_set) {
+      CU_TRY(cudaFuncSetAttribute(k_spgemm_warp_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem));
+      stage_set = true;
+    }
+    airg::note_launch(), k_spgemm_warp_staged<<<152 * 3, kStageWarps * 32, stage_smem, s>>>(g, mid, ctr + 0, big, ctr + 1);
     airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2);
     static bool smem_set = false;
     const size_t smem = sizeof(int) * (size_t)kBlockCapMax;
@@ -1080,23 +1481,49 @@ int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_dia
     airg::note_launch(), k_spgemm_block<<<152, 256, smem, s>>>(g, lng, ctr + 2, kBlockCapMax, ctr + 3);
     KERNEL_CHECK();
   }
+  out.nrows = ar;
+  out.ncols = Bc ? Bc->ncols : Bp->ncols;
+  out.total = total;
+  out.cnt = g.cnt;
+  out.tcol = g.tcol;
+  out.tval = g.tval;
+  out.err = ctr + 3;
+  out.beg = nullptr;
+  if (total <= 0x7fffffffLL) {  // 32-bit row starts, for use as the B operand of another product
+    AIRG_TRY(tmp.alloc(&out.beg, std::max(ar, 1)));
+    if (ar > 0) airg::note_launch(), k_i64_to_i32<<<GRID(ar)>>>(ar, out.ubo, out.beg);
+  }
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+// Compacts a padded product into CSR owned by `own`.
+int spgemm_compact(const SpgPadded& P, DCsr& out, Arena& own, Arena& tmp, cudaStream_t s) {
+  const int ar = P.nrows;
   int* rp;
   AIRG_TRY(own.alloc(&rp, (size_t)ar + 1));
   int err = 0;
-  CU_TRY(cudaMemcpyAsync(&err, ctr + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaMemcpyAsync(&err, P.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   long long nnz = 0;
-  AIRG_TRY(scan_i32(g.cnt, rp, ar, tmp, s, &nnz));  // synchronises: err is valid below
+  AIRG_TRY(scan_i32(P.cnt, rp, ar, tmp, s, &nnz));  // synchronises: err is valid below
   if (err) return AIRG_ERR_UNSUPPORTED;
   if (nnz > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
   out.nrows = ar;
-  out.ncols = B.ncols;
+  out.ncols = P.ncols;
   out.nnz = (int)nnz;
   out.rp = rp;
   AIRG_TRY(own.alloc(&out.ci, (size_t)nnz));
   AIRG_TRY(own.alloc(&out.v, (size_t)nnz));
-  if (ar > 0) airg::note_launch(), k_spgemm_copy<<<GRID(ar)>>>(ar, ubo, g.tcol, g.tval, rp, out.ci, out.v);
+  if (ar > 0) airg::note_launch(), k_spgemm_copy<<<(ar + 255) / 256, 256, 0, s>>>(ar, P.ubo, P.tcol, P.tval, rp, out.ci, out.v);
   KERNEL_CHECK();
   return AIRG_OK;
+}
+
+int spgemm(const DCsr& A, const DCsr& B, double scale, double tol, bool keep_diag, DCsr& out, Arena& own,
+           Arena& tmp, cudaStream_t s) {
+  SpgPadded P;
+  AIRG_TRY(spgemm_padded(A, &B, nullptr, scale, tol, keep_diag, P, tmp, s));
+  return spgemm_compact(P, out, own, tmp, s);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1110,13 +1537,13 @@ __global__ void k_one_point(int n, const int* __restrict__ rp, const int* __rest
     const int i = (int)ii;
     if (cf[i] != kF) continue;
     int best = -1;
-    double bv = -1.0;
+    long long bv = -1;  // |a_ij| as bits
     for (int pass = 0; pass < 2 && best < 0; ++pass)
       for (int k = rp[i]; k < rp[i + 1]; ++k) {
         const int j = ci[k];
-        if (j == i || cf[j] != kC || v[k] == 0.0) continue;
+        const long long a = abs_bits(v[k]);
+        if (j == i || cf[j] != kC || a == 0) continue;
         if (pass == 0 && !strong[k]) continue;
-        const double a = fabs(v[k]);
         if (a > bv) { bv = a; best = j; }
       }
     w[fpos[i]] = best >= 0 ? best - fpos[best] : -1;
@@ -1187,7 +1614,8 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
     L.nc = 0;
     L.m = mc;
     AIRG_TRY(own.alloc(&L.alpha, mc));
-    AIRG_TRY(poly_fit(A, mc, p.seed, level, L.alpha, &L.fitted, tmp, s));
+    AIRG_TRY(own.alloc(&L.fitted_dev, 1));
+    AIRG_TRY(poly_fit(A, mc, p.seed, level, L.alpha, L.fitted_dev, tmp, s));
     AIRG_TRY(fixed_sparsity_inverse(A, L.alpha, mc, L.Ainv, own, tmp, s));
     mark(2);
     mark(3);
@@ -1212,16 +1640,21 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(tmp.alloc(&cCF, nc));
   airg::note_launch(), k_extract_count<<<GRID(n)>>>(n, A.rp, A.ci, L.cf, fpos, cFF, cFC, cCF);
   KERNEL_CHECK();
-  long long zff, zfc, zcf;
   L.Aff.nrows = nf; L.Aff.ncols = nf;
   L.Afc.nrows = nf; L.Afc.ncols = nc;
   L.Acf.nrows = nc; L.Acf.ncols = nf;
   AIRG_TRY(own.alloc(&L.Aff.rp, (size_t)nf + 1));
   AIRG_TRY(own.alloc(&L.Afc.rp, (size_t)nf + 1));
   AIRG_TRY(own.alloc(&L.Acf.rp, (size_t)nc + 1));
-  AIRG_TRY(scan_i32(cFF, L.Aff.rp, nf, tmp, s, &zff));
-  AIRG_TRY(scan_i32(cFC, L.Afc.rp, nf, tmp, s, &zfc));
-  AIRG_TRY(scan_i32(cCF, L.Acf.rp, nc, tmp, s, &zcf));
+  AIRG_TRY(scan_i32(cFF, L.Aff.rp, nf, tmp, s, nullptr));
+  AIRG_TRY(scan_i32(cFC, L.Afc.rp, nf, tmp, s, nullptr));
+  AIRG_TRY(scan_i32(cCF, L.Acf.rp, nc, tmp, s, nullptr));
+  int tot[3];
+  CU_TRY(cudaMemcpyAsync(tot + 0, L.Aff.rp + nf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaMemcpyAsync(tot + 1, L.Afc.rp + nf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaMemcpyAsync(tot + 2, L.Acf.rp + nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU_TRY(cudaStreamSynchronize(s));
+  const long long zff = tot[0], zfc = tot[1], zcf = tot[2];
   L.Aff.nnz = (int)zff; L.Afc.nnz = (int)zfc; L.Acf.nnz = (int)zcf;
   AIRG_TRY(own.alloc(&L.Aff.ci, zff)); AIRG_TRY(own.alloc(&L.Aff.v, zff));
   AIRG_TRY(own.alloc(&L.Afc.ci, zfc)); AIRG_TRY(own.alloc(&L.Afc.v, zfc));
@@ -1232,7 +1665,8 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   // steps 3-8
   L.m = m;
   AIRG_TRY(own.alloc(&L.alpha, m));
-  AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, &L.fitted, tmp, s));
+  AIRG_TRY(own.alloc(&L.fitted_dev, 1));
+  AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, L.fitted_dev, tmp, s));
   AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s));
   mark(3);
   // step 9
@@ -1255,8 +1689,9 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(tmp.alloc(&P.v, n));
   airg::note_launch(), k_P_fill<<<GRID(n)>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
   KERNEL_CHECK();
-  DCsr AP;
-  AIRG_TRY(spgemm(A, P, 1.0, 0.0, false, AP, tmp, tmp, s));
+  // A P stays in the padded form of the product (no compaction): R reads its rows in place
+  SpgPadded AP;
+  AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, tmp, s));
   DCsr R;
   R.nrows = nc; R.ncols = n; R.nnz = L.Z.nnz + nc;
   AIRG_TRY(tmp.alloc(&R.rp, (size_t)nc + 1));
@@ -1264,7 +1699,18 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(tmp.alloc(&R.v, R.nnz));
   if (nc > 0) airg::note_launch(), k_R_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, L.Fnat, L.Cnat, R.rp, R.ci, R.v);
   KERNEL_CHECK();
-  AIRG_TRY(spgemm(R, AP, 1.0, p.drop_Ac, true, Ac_out, own, tmp, s));
+  if (AP.beg) {
+    SpgPadded RAP;
+    AIRG_TRY(spgemm_padded(R, nullptr, &AP, 1.0, p.drop_Ac, true, RAP, tmp, s));
+    int ap_err = 0;
+    CU_TRY(cudaMemcpyAsync(&ap_err, AP.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AIRG_TRY(spgemm_compact(RAP, Ac_out, own, tmp, s));  // synchronises: ap_err is valid below
+    if (ap_err) return AIRG_ERR_UNSUPPORTED;
+  } else {
+    DCsr APc;
+    AIRG_TRY(spgemm_compact(AP, APc, tmp, tmp, s));
+    AIRG_TRY(spgemm(R, APc, 1.0, p.drop_Ac, true, Ac_out, own, tmp, s));
+  }
   mark(5);
   return AIRG_OK;
 }
