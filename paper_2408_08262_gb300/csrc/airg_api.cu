@@ -111,6 +111,31 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     Arena& a;
     ~LtRel() { a.release(); }
   } ltrel{lt};
+  // side stream for the work of a level that does not wait for its polynomial
+  Arena lt2;
+  lt2.chunk_min = (size_t)256 << 20;
+  SideStream side;
+  side.tmp = &lt2;
+  struct SideRel {
+    SideStream& sd;
+    Arena& a;
+    ~SideRel() {
+      if (sd.s) cudaStreamSynchronize(sd.s);
+      a.release();
+      if (sd.s) cudaStreamSynchronize(sd.s);
+      if (sd.fork) cudaEventDestroy(sd.fork);
+      if (sd.join) cudaEventDestroy(sd.join);
+      if (sd.s) cudaStreamDestroy(sd.s);
+    }
+  } siderel{side, lt2};
+  if (cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (side.s) cudaStreamDestroy(side.s);
+    side.s = nullptr;  // run everything on s
+  }
+  lt2.s = side.s ? side.s : s;
   for (int l = 0;; ++l) {
     LevelBuild L;
     for (int k = 0; k < 6; ++k)
@@ -118,7 +143,8 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
       else { L.ev[k] = nullptr; cudaGetLastError(); }
     DCsr Ac;
     lt.reset();
-    int rc = build_level(A, sp, l, l == sp.max_levels - 1, L, Ac, H->setup_mem, lt, s);
+    lt2.reset();
+    int rc = build_level(A, sp, l, l == sp.max_levels - 1, L, Ac, H->setup_mem, lt, s, side.s ? &side : nullptr);
     if (rc != AIRG_OK) return rc;
     H->lb.push_back(L);
     if (L.coarsest) break;

@@ -158,7 +158,7 @@ void dev_cast_d2bf(const double* in, void* out, long long n, cudaStream_t s);
 void dev_cast_f2d(const float* in, double* out, long long n, cudaStream_t s);
 void dev_gather_prolong_f(float* x, int nf, const int* w, cudaStream_t s);
 
-void dev_scale(const double* x, double alpha_div, double* y, int n, cudaStream_t s);  // y = x / a
+void dev_scale(const double* x, double alpha_div, double* y, int n, cudaStream_t s);  // y = x * (1 / a)
 void dev_permute(const double* in, const int* pos, double* out, int n, bool inverse, cudaStream_t s);
 void dev_gather_prolong(double* x, int nf, const int* w, cudaStream_t s);  // x[f] = x[nf + w[f]]
 void dev_fill(double* x, double v, int n, cudaStream_t s);
@@ -224,10 +224,19 @@ struct LevelBuild {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
+// A second stream for work of a level that does not depend on the polynomial (the one-point
+// prolongator and A P), with its own scratch arena and two events (fork, join).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  Arena* tmp = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 // Builds level data and the next coarse matrix (setup steps 1-11).  If the level turns out to be
-// the coarsest, only the polynomial is built and *Ac_out is left empty.
+// the coarsest, only the polynomial is built and *Ac_out is left empty.  With `side`, the one-point
+// prolongator and A P run on the side stream while the polynomial is fitted on s.
 int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coarsest, LevelBuild& L,
-                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s);
+                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s, const SideStream* side = nullptr);
 
 // Nested solve numbering of a non-coarsest level from its F/C positions and the next level's
 // nested numbering (nullptr when the next level is the coarsest: identity there).

@@ -457,12 +457,14 @@ int pick_lanes(double L) {
 // ------------------------------------------------------------------------------------------
 // Small vector kernels
 // ------------------------------------------------------------------------------------------
-__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int n) {
+// y = x * (1/a): one multiply per element (an FP64 division per element would make this kernel
+// bound by sm_103a's FP64 rate instead of by bandwidth)
+__global__ void k_scale(const double* __restrict__ x, double inv, double* __restrict__ y, int n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = x[i] / a;
+    y[i] = x[i] * inv;
 }
 void dev_scale(const double* x, double a, double* y, int n, cudaStream_t s) {
-  if (n > 0) airg::note_launch(), k_scale<<<grid_for(n, 256), 256, 0, s>>>(x, a, y, n);
+  if (n > 0) airg::note_launch(), k_scale<<<grid_for(n, 256), 256, 0, s>>>(x, 1.0 / a, y, n);
 }
 
 __global__ void k_permute(const double* __restrict__ in, const int* __restrict__ pos, double* __restrict__ out, int n,

@@ -1587,7 +1587,7 @@ __global__ void k_R_fill(int nc, const int* __restrict__ zrp, const int* __restr
 }
 
 int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coarsest, LevelBuild& L,
-                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s) {
+                DCsr& Ac_out, Arena& own, Arena& tmp, cudaStream_t s, const SideStream* side) {
   const int n = A.nrows;
   L.A = A;
   L.n = n;
@@ -1662,36 +1662,46 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   airg::note_launch(), k_extract_fill<<<GRID(n)>>>(n, A.rp, A.ci, A.v, L.cf, fpos, L.Aff, L.Afc, L.Acf);
   KERNEL_CHECK();
   mark(2);
-  // steps 3-8
+  // steps 3-8 on s (no host synchronisation inside)
   L.m = m;
   AIRG_TRY(own.alloc(&L.alpha, m));
   AIRG_TRY(own.alloc(&L.fitted_dev, 1));
   AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, L.fitted_dev, tmp, s));
   AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s));
+  // steps 10-11a (one-point P and A P) need only the splitting: on the side stream, they overlap
+  // the polynomial fit
+  AIRG_TRY(own.alloc(&L.w, nf));
+  cudaStream_t s2 = s;
+  Arena* tmp2 = &tmp;
+  if (side && side->s) {
+    CU_TRY(cudaEventRecord(side->fork, s));
+    CU_TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+    s2 = side->s;
+    tmp2 = side->tmp;
+  }
+  airg::note_launch(), k_one_point<<<grid_for(n, 256), 256, 0, s2>>>(n, A.rp, A.ci, A.v, strong, L.cf, fpos, L.w);
+  KERNEL_CHECK();
+  DCsr P;
+  P.nrows = n; P.ncols = nc;
+  int* pc;
+  AIRG_TRY(tmp2->alloc(&pc, n));
+  AIRG_TRY(tmp2->alloc(&P.rp, (size_t)n + 1));
+  airg::note_launch(), k_P_count<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, pc);
+  AIRG_TRY(scan_i32(pc, P.rp, n, *tmp2, s2, nullptr));
+  P.nnz = n;  // upper bound (only P.rp delimits rows); avoids a synchronisation
+  AIRG_TRY(tmp2->alloc(&P.ci, n));
+  AIRG_TRY(tmp2->alloc(&P.v, n));
+  airg::note_launch(), k_P_fill<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
+  KERNEL_CHECK();
+  // A P stays in the padded form of the product (no compaction): R reads its rows in place
+  SpgPadded AP;
+  AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, *tmp2, s2));
+  if (s2 != s) CU_TRY(cudaEventRecord(side->join, s2));
   mark(3);
   // step 9
   AIRG_TRY(spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false, L.Z, own, tmp, s));
   mark(4);
-  // step 10
-  AIRG_TRY(own.alloc(&L.w, nf));
-  airg::note_launch(), k_one_point<<<GRID(n)>>>(n, A.rp, A.ci, A.v, strong, L.cf, fpos, L.w);
-  KERNEL_CHECK();
-  // step 11: A_c = R (A P)
-  DCsr P;
-  P.nrows = n; P.ncols = nc;
-  int* pc;
-  AIRG_TRY(tmp.alloc(&pc, n));
-  AIRG_TRY(tmp.alloc(&P.rp, (size_t)n + 1));
-  airg::note_launch(), k_P_count<<<GRID(n)>>>(n, L.cf, fpos, L.w, pc);
-  AIRG_TRY(scan_i32(pc, P.rp, n, tmp, s, nullptr));
-  P.nnz = n;  // upper bound (only P.rp delimits rows); avoids a synchronisation
-  AIRG_TRY(tmp.alloc(&P.ci, n));
-  AIRG_TRY(tmp.alloc(&P.v, n));
-  airg::note_launch(), k_P_fill<<<GRID(n)>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
-  KERNEL_CHECK();
-  // A P stays in the padded form of the product (no compaction): R reads its rows in place
-  SpgPadded AP;
-  AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, tmp, s));
+  // step 11b: A_c = R (A P)
   DCsr R;
   R.nrows = nc; R.ncols = n; R.nnz = L.Z.nnz + nc;
   AIRG_TRY(tmp.alloc(&R.rp, (size_t)nc + 1));
@@ -1699,6 +1709,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(tmp.alloc(&R.v, R.nnz));
   if (nc > 0) airg::note_launch(), k_R_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, L.Fnat, L.Cnat, R.rp, R.ci, R.v);
   KERNEL_CHECK();
+  if (s2 != s) CU_TRY(cudaStreamWaitEvent(s, side->join, 0));
   if (AP.beg) {
     SpgPadded RAP;
     AIRG_TRY(spgemm_padded(R, nullptr, &AP, 1.0, p.drop_Ac, true, RAP, tmp, s));
