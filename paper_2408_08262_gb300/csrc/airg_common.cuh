@@ -125,7 +125,7 @@ struct Reducer {
   double* partial = nullptr;  // [kRedBlocks * kRedCols]
   unsigned* counter = nullptr;
 };
-constexpr int kRedBlocks = 304;
+constexpr int kRedBlocks = 152 * 8;  // 8 CTAs of 256 threads per SM: enough loads in flight for HBM
 constexpr int kRedCols = 34;
 int reducer_init(Reducer& r, Arena& a, cudaStream_t s);
 

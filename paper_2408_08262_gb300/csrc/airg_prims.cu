@@ -137,7 +137,7 @@ int reducer_init(Reducer& r, Arena& a, cudaStream_t s) {
 }
 
 // Reduces acc[0..nv) across the block, writes the block's partials, and lets the last block to
-// finish sum all partials in block order into out[0..nv).  Fixed grid => deterministic.
+// finish sum all partials (in a fixed order) into out[0..nv).  Fixed grid => deterministic.
 template <int NV>
 __device__ void block_partials_finish(const double (&acc)[NV], int nv, double* partial, unsigned* counter,
                                       double* out0, int nout0, double* out1) {
@@ -166,13 +166,18 @@ __device__ void block_partials_finish(const double (&acc)[NV], int nv, double* p
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+  // one warp per value: lane l sums the partials of blocks l, l+32, ... in order, then a fixed
+  // butterfly (short FP64 chains: FP64 latency on sm_103a is tens of clocks per add)
+  for (int k = wid; k < nv; k += nw) {
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += ((volatile double*)partial)[(size_t)b * kRedCols + k];
-    if (k < nout0) {
-      if (out0) out0[k] = t;
-    } else if (out1) {
-      out1[0] = t;
+    for (unsigned b = lane; b < gridDim.x; b += 32) t += ((volatile double*)partial)[(size_t)b * kRedCols + k];
+    t = warp_sum(t);
+    if (lane == 0) {
+      if (k < nout0) {
+        if (out0) out0[k] = t;
+      } else if (out1) {
+        out1[0] = t;
+      }
     }
   }
   if (threadIdx.x == 0) *counter = 0u;
@@ -198,11 +203,12 @@ template <int NC>
 __global__ void __launch_bounds__(256) k_gs_pass(const double* __restrict__ V, long long ldv, int ncols,
                                                  double* __restrict__ w, int n, const double* __restrict__ hsub,
                                                  double* dots, double* nrm, double* partial, unsigned* counter) {
+  (void)ncols;  // == NC
   __shared__ double sh[NC];
   if (hsub)
-    for (int k = threadIdx.x; k < ncols; k += blockDim.x) sh[k] = hsub[k];
+    for (int k = threadIdx.x; k < NC; k += blockDim.x) sh[k] = hsub[k];
   __syncthreads();
-  const int nd = dots ? ncols : 0;  // dot products wanted
+  const bool want = dots != nullptr;  // dot products wanted
   double acc[NC + 1];
 #pragma unroll
   for (int k = 0; k <= NC; ++k) acc[k] = 0.0;
@@ -210,38 +216,52 @@ __global__ void __launch_bounds__(256) k_gs_pass(const double* __restrict__ V, l
     double wr = w[r];
     double vk[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) vk[k] = (k < ncols && (hsub || k < nd)) ? V[(size_t)k * ldv + r] : 0.0;
+    for (int k = 0; k < NC; ++k) vk[k] = V[(size_t)k * ldv + r];
     if (hsub) {
-      double sub = 0.0;
+      // two interleaved partial sums halve the dependent FP64 chain
+      double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-      for (int k = 0; k < NC; ++k)
-        if (k < ncols) sub += vk[k] * sh[k];
-      wr -= sub;
+      for (int k = 0; k < NC; k += 2) {
+        s0 = fma(vk[k], sh[k], s0);
+        if (k + 1 < NC) s1 = fma(vk[k + 1], sh[k + 1], s1);
+      }
+      wr -= s0 + s1;
       w[r] = wr;
     }
+    if (want) {
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
-      if (k < nd) acc[k] += vk[k] * wr;
-    acc[NC] += wr * wr;
+      for (int k = 0; k < NC; ++k) acc[k] = fma(vk[k], wr, acc[k]);
+    }
+    acc[NC] = fma(wr, wr, acc[NC]);
   }
-  // place the norm accumulator right after the nd dots so one finish call reduces nd+1 values
-#pragma unroll
-  for (int k = 0; k < NC; ++k)
-    if (k == nd) acc[k] = acc[NC];
+  // place the norm accumulator right after the dots so one finish call reduces nd+1 values
+  const int nd = want ? NC : 0;
+  if (!want) acc[0] = acc[NC];
   block_partials_finish<NC + 1>(acc, nd + 1, partial, counter, dots, nd, nrm);
+}
+
+// One instance per column count, so no FP64 instruction is spent on absent columns (sm_103a's FP64
+// issue rate, not HBM, bounds these passes).
+template <int NC>
+static void gs_launch(const double* V, long long ldv, int ncols, double* w, int n, const double* hsub, double* dots,
+                      double* nrm, Reducer& r, cudaStream_t s) {
+  airg::note_launch(), k_gs_pass<NC><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
 }
 
 int dev_gs_pass(const double* V, long long ldv, int ncols, double* w, int n, const double* hsub, double* dots,
                 double* nrm, Reducer& r, cudaStream_t s) {
-  if (ncols < 1 || ncols > 32) return AIRG_ERR_ARG;
-  if (ncols <= 4)
-    airg::note_launch(), k_gs_pass<4><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
-  else if (ncols <= 8)
-    airg::note_launch(), k_gs_pass<8><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
-  else if (ncols <= 16)
-    airg::note_launch(), k_gs_pass<16><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
-  else
-    airg::note_launch(), k_gs_pass<32><<<kRedBlocks, 256, 0, s>>>(V, ldv, ncols, w, n, hsub, dots, nrm, r.partial, r.counter);
+  switch (ncols) {
+#define AIRG_GS_CASE(c) \
+  case c: gs_launch<c>(V, ldv, ncols, w, n, hsub, dots, nrm, r, s); break;
+    AIRG_GS_CASE(1) AIRG_GS_CASE(2) AIRG_GS_CASE(3) AIRG_GS_CASE(4) AIRG_GS_CASE(5) AIRG_GS_CASE(6)
+    AIRG_GS_CASE(7) AIRG_GS_CASE(8) AIRG_GS_CASE(9) AIRG_GS_CASE(10) AIRG_GS_CASE(11) AIRG_GS_CASE(12)
+    AIRG_GS_CASE(13) AIRG_GS_CASE(14) AIRG_GS_CASE(15) AIRG_GS_CASE(16) AIRG_GS_CASE(17) AIRG_GS_CASE(18)
+    AIRG_GS_CASE(19) AIRG_GS_CASE(20) AIRG_GS_CASE(21) AIRG_GS_CASE(22) AIRG_GS_CASE(23) AIRG_GS_CASE(24)
+    AIRG_GS_CASE(25) AIRG_GS_CASE(26) AIRG_GS_CASE(27) AIRG_GS_CASE(28) AIRG_GS_CASE(29) AIRG_GS_CASE(30)
+    AIRG_GS_CASE(31) AIRG_GS_CASE(32)
+#undef AIRG_GS_CASE
+    default: return AIRG_ERR_ARG;
+  }
   KERNEL_CHECK();
   return AIRG_OK;
 }

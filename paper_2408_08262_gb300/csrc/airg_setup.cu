@@ -85,6 +85,10 @@ int validate_csr(const DCsr& A, Arena& tmp, cudaStream_t s) {
 // sm_103a) with results identical to the FP64 comparisons.
 __device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
 
+// Row kernels walk their entries in batches of kGB: the batch's column loads, then its gathers of
+// per-column state, are issued together (two memory latencies per batch instead of two per entry).
+constexpr int kGB = 4;
+
 __global__ void k_strength(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
                            double alpha, uint8_t* __restrict__ strong, int* __restrict__ nS) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -155,14 +159,37 @@ __global__ void k_pmisr_select(int n, const int* __restrict__ rp, const int* __r
     if (cf[i] == 0) {
       const long long wi = __double_as_longlong(w[i]);
       bool mn = true;
-      for (int k = rp[i]; k < rp[i + 1] && mn; ++k) {
-        if (!strong[k]) continue;
-        const int j = ci[k];
-        if (cf[j] == 0 && !pmisr_less(wi, i, __double_as_longlong(w[j]), j)) mn = false;
+      const int e = rp[i + 1];
+      for (int k0 = rp[i]; k0 < e && mn; k0 += kGB) {
+        int j[kGB];
+        int8_t c[kGB];
+        long long wj[kGB];
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < e && strong[k0 + t]) ? ci[k0 + t] : -1;
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) {
+          c[t] = (j[t] >= 0) ? cf[j[t]] : (int8_t)1;
+          wj[t] = (j[t] >= 0) ? __double_as_longlong(w[j[t]]) : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < kGB; ++t)
+          if (c[t] == 0 && !pmisr_less(wi, i, wj[t], j[t])) mn = false;
       }
-      for (int k = rpT[i]; k < rpT[i + 1] && mn; ++k) {
-        const int j = colT[k];
-        if (cf[j] == 0 && !pmisr_less(wi, i, __double_as_longlong(w[j]), j)) mn = false;
+      const int eT = rpT[i + 1];
+      for (int k0 = rpT[i]; k0 < eT && mn; k0 += kGB) {
+        int j[kGB];
+        int8_t c[kGB];
+        long long wj[kGB];
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < eT) ? colT[k0 + t] : -1;
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) {
+          c[t] = (j[t] >= 0) ? cf[j[t]] : (int8_t)1;
+          wj[t] = (j[t] >= 0) ? __double_as_longlong(w[j[t]]) : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < kGB; ++t)
+          if (c[t] == 0 && !pmisr_less(wi, i, wj[t], j[t])) mn = false;
       }
       isD = mn;
     }
@@ -180,10 +207,24 @@ __global__ void k_pmisr_apply(int n, const int* __restrict__ rp, const int* __re
     if (cf[i] != 0) continue;
     if (D[i]) { cf[i] = kF; continue; }
     bool nbD = false;
-    for (int k = rp[i]; k < rp[i + 1] && !nbD; ++k)
-      if (strong[k] && D[ci[k]]) nbD = true;
-    for (int k = rpT[i]; k < rpT[i + 1] && !nbD; ++k)
-      if (D[colT[k]]) nbD = true;
+    const int e = rp[i + 1];
+    for (int k0 = rp[i]; k0 < e && !nbD; k0 += kGB) {
+      int j[kGB];
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < e && strong[k0 + t]) ? ci[k0 + t] : -1;
+#pragma unroll
+      for (int t = 0; t < kGB; ++t)
+        if (j[t] >= 0 && D[j[t]]) nbD = true;
+    }
+    const int eT = rpT[i + 1];
+    for (int k0 = rpT[i]; k0 < eT && !nbD; k0 += kGB) {
+      int j[kGB];
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < eT) ? colT[k0 + t] : -1;
+#pragma unroll
+      for (int t = 0; t < kGB; ++t)
+        if (j[t] >= 0 && D[j[t]]) nbD = true;
+    }
     if (nbD) cf[i] = kC;
     else left++;
   }
@@ -209,12 +250,25 @@ __global__ void k_ddc_theta(int n, const int* __restrict__ rp, const int* __rest
     double th = 0.0;
     if (cf[i] == kF) {
       double sum = 0.0, d = 0.0;
-      for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const int j = ci[k];
-        if (j == i) d = fabs(v[k]);
-        else if (cf[j] == kF) sum += fabs(v[k]);
-      }
-      th = (sum == 0.0) ? 0.0 : sum / d;
+      const int e = rp[i + 1];
+      // batches of kGB entries: the column loads, then the gathers, are issued together
+      for (int k0 = rp[i]; k0 < e; k0 += kGB) {
+        int j[kGB];
+        double a[kGB];
+        int8_t f[kGB];
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < e) ? ci[k0 + t] : -1;
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) {
+          a[t] = (j[t] >= 0) ? v[k0 + t] : 0.0;
+          f[t] = (j[t] >= 0) ? cf[j[t]] : (int8_t)0;
+        }
+#pragma unroll
+        for (int t = 0; t < kGB; ++t) {
+          if (j[t] == i) d = fabs(a[t]);
+          else if (j[t] >= 0 && f[t] == kF) sum += fabs(a[t]);
+        }
+      }      th = (sum == 0.0) ? 0.0 : sum / d;
       nf++;
       nc += (th != 0.0);
     }
@@ -385,9 +439,17 @@ __global__ void k_extract_count(int n, const int* __restrict__ rp, const int* __
   for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
     const int i = (int)ii;
     int nFcol = 0, nCcol = 0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      if (cf[ci[k]] == kF) nFcol++;
-      else nCcol++;
+    const int e = rp[i + 1];
+    for (int k0 = rp[i]; k0 < e; k0 += kGB) {
+      int j[kGB];
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < e) ? ci[k0 + t] : -1;
+#pragma unroll
+      for (int t = 0; t < kGB; ++t)
+        if (j[t] >= 0) {
+          if (cf[j[t]] == kF) nFcol++;
+          else nCcol++;
+        }
     }
     const int fp = fpos[i];
     if (cf[i] == kF) { cFF[fp] = nFcol; cFC[fp] = nCcol; }
@@ -399,19 +461,32 @@ __global__ void k_extract_fill(int n, const int* __restrict__ rp, const int* __r
   for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
     const int i = (int)ii;
     const int fp = fpos[i];
-    if (cf[i] == kF) {
-      int a = Aff.rp[fp], b = Afc.rp[fp];
-      for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const int j = ci[k];
-        const int fj = fpos[j];
-        if (cf[j] == kF) { Aff.ci[a] = fj; Aff.v[a++] = v[k]; }
-        else { Afc.ci[b] = j - fj; Afc.v[b++] = v[k]; }
+    const bool rowF = cf[i] == kF;
+    int a = rowF ? Aff.rp[fp] : Acf.rp[i - fp];
+    int b = rowF ? Afc.rp[fp] : 0;
+    const int e = rp[i + 1];
+    for (int k0 = rp[i]; k0 < e; k0 += kGB) {
+      int j[kGB], fj[kGB];
+      int8_t c[kGB];
+      double vv[kGB];
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) j[t] = (k0 + t < e) ? ci[k0 + t] : -1;
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) {
+        c[t] = (j[t] >= 0) ? cf[j[t]] : (int8_t)0;
+        fj[t] = (j[t] >= 0) ? fpos[j[t]] : 0;
+        vv[t] = (j[t] >= 0) ? v[k0 + t] : 0.0;
       }
-    } else {
-      int a = Acf.rp[i - fp];
-      for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const int j = ci[k];
-        if (cf[j] == kF) { Acf.ci[a] = fpos[j]; Acf.v[a++] = v[k]; }
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) {
+        if (j[t] < 0) continue;
+        if (rowF) {
+          if (c[t] == kF) { Aff.ci[a] = fj[t]; Aff.v[a++] = vv[t]; }
+          else { Afc.ci[b] = j[t] - fj[t]; Afc.v[b++] = vv[t]; }
+        } else if (c[t] == kF) {
+          Acf.ci[a] = fj[t];
+          Acf.v[a++] = vv[t];
+        }
       }
     }
   }
