@@ -286,16 +286,77 @@ CfDetail cf_split(const Csr& A, const Params& p, int level) {
 // GMRES polynomial (Section "AIRG", setup steps 3-8)
 // ---------------------------------------------------------------------------------------------
 
-// Step 3: normally distributed rhs by the Box-Muller transform: for entry i,
-// u1 = 1 - r(2i), u2 = r(2i+1), z = sqrt(-2 ln u1) cos(2 pi u2).
+// Step 3: normally distributed rhs (zero mean) by the Box-Muller transform in single precision:
+// for entry i, k1 and k2 are the top 24 bits of outputs 2i and 2i+1 of stream 1,
+// u1 = 1 - k1 2^-24 (in (0, 1]), u2 = k2 2^-24, z = sqrt(-2 ln u1) cos(2 pi u2).  ln and cos are
+// evaluated by the fixed float sequences below, so that every implementation following them
+// draws the same vector bit for bit; the paper asks only for a normally distributed rhs.
+uint32_t unif24(uint64_t key, uint64_t c) { return (uint32_t)(mix64(key + kGamma * (c + 1)) >> 40); }
+
+// ln x, x in (0, 1] normal: x = m 2^e with m in [1, 2), halved (e + 1) above sqrt 2; with f = m - 1
+// and s = f / (2 + f), ln(1 + f) = 2 atanh s = 2 (s + s^3/3 + s^5/5 + ...) (Abramowitz & Stegun
+// 4.1.28), here to s^11, by Horner in z = s^2; e ln 2 is added with ln 2 split in a short high
+// part (exact products e * hi) and a low part.
+float ln_f32(float x) {
+  uint32_t bits;
+  std::memcpy(&bits, &x, 4);
+  int e = (int)(bits >> 23) - 127;
+  uint32_t mbits = (bits & 0x7fffffu) | 0x3f800000u;
+  float m;
+  std::memcpy(&m, &mbits, 4);
+  if (m > 0x1.6a09e6p+0f) {  // sqrt 2
+    m = m * 0.5f;
+    e += 1;
+  }
+  const float f = m - 1.0f;
+  const float s = f / (2.0f + f);
+  const float z = s * s;
+  float p = std::fmaf(z, 0x1.745d18p-3f, 0x1.c71c72p-3f);  // 2/11, 2/9
+  p = std::fmaf(z, p, 0x1.24924ap-2f);                     // 2/7
+  p = std::fmaf(z, p, 0x1.99999ap-2f);                     // 2/5
+  p = std::fmaf(z, p, 0x1.555556p-1f);                     // 2/3
+  const float sz = s * z;
+  const float r = std::fmaf(sz, p, 2.0f * s);
+  const float ef = (float)e;
+  return std::fmaf(ef, 0x1.62e4p-1f, std::fmaf(ef, 0x1.7f7d1cp-20f, r));  // ln 2 = hi + lo
+}
+
+// cos(2 pi k 2^-24), k < 2^24: the nearest quarter turn q is removed exactly in integers, leaving
+// x = 2 pi r with |r| <= 1/8; cos x and sin x by their Taylor series (to x^10 and x^9) by Horner in
+// x^2, and cos(x + q pi/2) picked by q mod 4.
+float cos2pi_f32(uint32_t k) {
+  const uint32_t q = (k + (1u << 21)) >> 22;
+  const int32_t ri = (int32_t)k - (int32_t)(q << 22);
+  const float r = (float)ri * 0x1p-24f;
+  const float x = r * 0x1.921fb6p+2f;  // 2 pi
+  const float x2 = x * x;
+  float c = std::fmaf(x2, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);  // -1/10!, 1/8!
+  c = std::fmaf(x2, c, -0x1.6c16c2p-10f);                      // -1/6!
+  c = std::fmaf(x2, c, 0x1.555556p-5f);                        // 1/4!
+  c = std::fmaf(x2, c, -0.5f);
+  c = std::fmaf(x2, c, 1.0f);
+  float sn = std::fmaf(x2, 0x1.71de3ap-19f, -0x1.a01a02p-13f);  // 1/9!, -1/7!
+  sn = std::fmaf(x2, sn, 0x1.111112p-7f);                       // 1/5!
+  sn = std::fmaf(x2, sn, -0x1.555556p-3f);                      // -1/3!
+  const float x3 = x * x2;
+  sn = std::fmaf(x3, sn, x);
+  switch (q & 3u) {
+    case 0: return c;
+    case 1: return -sn;
+    case 2: return -c;
+    default: return sn;
+  }
+}
+
 std::vector<double> box_muller(uint64_t seed, int level, int n) {
   std::vector<double> z(n);
   uint64_t key = stream_key(seed, level, 1);
-  const double two_pi = 6.283185307179586;
   for (int i = 0; i < n; ++i) {
-    double u1 = 1.0 - unif01(key, 2 * (uint64_t)i);
-    double u2 = unif01(key, 2 * (uint64_t)i + 1);
-    z[i] = std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+    const uint32_t k1 = unif24(key, 2 * (uint64_t)i);
+    const uint32_t k2 = unif24(key, 2 * (uint64_t)i + 1);
+    const float u1 = 1.0f - (float)k1 * 0x1p-24f;
+    const float t = -2.0f * ln_f32(u1);
+    z[i] = (double)(std::sqrt(t) * cos2pi_f32(k2));
   }
   return z;
 }
@@ -996,6 +1057,11 @@ int oracle_box_muller(unsigned long long seed, int level, int n, double* z) {
   return 0;
 }
 
+int oracle_unif24(unsigned long long seed, int level, int stream, int n, unsigned int* r) {
+  uint64_t key = stream_key(seed, level, stream);
+  for (int i = 0; i < n; ++i) r[i] = unif24(key, (uint64_t)i);
+  return 0;
+}
 int oracle_unif01(unsigned long long seed, int level, int stream, int n, double* r) {
   uint64_t key = stream_key(seed, level, stream);
   for (int i = 0; i < n; ++i) r[i] = unif01(key, (uint64_t)i);

@@ -240,6 +240,13 @@ def box_muller(seed: int, level: int, n: int):
     return z
 
 
+def unif24(seed: int, level: int, stream: int, n: int):
+    """Top 24 bits of the first n outputs of a SplitMix64 stream (the Box-Muller draws)."""
+    r = np.zeros(n, dtype=np.uint32)
+    lib().oracle_unif24(C.c_ulonglong(seed), C.c_int(level), C.c_int(stream), C.c_int(n), r.ctypes.data_as(C.c_void_p))
+    return r
+
+
 def unif01(seed: int, level: int, stream: int, n: int):
     r = np.zeros(n)
     lib().oracle_unif01(C.c_ulonglong(seed), C.c_int(level), C.c_int(stream), C.c_int(n), r.ctypes.data_as(C.c_void_p))

@@ -495,13 +495,61 @@ __global__ void k_extract_fill(int n, const int* __restrict__ rp, const int* __r
 // ------------------------------------------------------------------------------------------
 // Steps 3-6: GMRES polynomial coefficients
 // ------------------------------------------------------------------------------------------
-// Box-Muller: entry i uses u1 = 1 - r(2i), u2 = r(2i+1): z = sqrt(-2 ln u1) cos(2 pi u2).
+// Box-Muller rhs in single precision (the paper asks for a normally distributed rhs of zero mean;
+// FP64 log and cos would cost this kernel ~50 FP64 instructions per entry on sm_103a).  Entry i
+// takes the top 24 bits k1, k2 of stream outputs 2i and 2i+1: u1 = 1 - k1 2^-24, u2 = k2 2^-24,
+// z = sqrt(-2 ln u1) cos(2 pi u2), with ln and cos by fixed float sequences (written with
+// explicitly rounded intrinsics, so no contraction changes them):
+//  - ln x: x = m 2^e, m in [1, 2) halved above sqrt 2; f = m - 1, s = f / (2 + f);
+//    ln(1 + f) = 2 atanh s = 2 (s + s^3/3 + ... + s^11/11) (Abramowitz & Stegun 4.1.28), Horner in
+//    s^2; plus e ln 2 with ln 2 split into a short high part and a low part.
+//  - cos 2 pi u: the nearest quarter turn q is removed in integers (|r| <= 1/8), x = 2 pi r;
+//    Taylor series of cos (to x^10) and sin (to x^9) in x^2; cos(x + q pi/2) by q mod 4.
+__device__ __forceinline__ uint32_t sm64_u24(uint64_t key, uint64_t c) {
+  return (uint32_t)(sm64_mix(key + kGamma * (c + 1)) >> 40);
+}
+__device__ __forceinline__ float bm_ln(float x) {
+  const uint32_t bits = __float_as_uint(x);
+  int e = (int)(bits >> 23) - 127;
+  float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float f = __fsub_rn(m, 1.0f);
+  const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
+  const float z = __fmul_rn(s, s);
+  float p = __fmaf_rn(z, 0x1.745d18p-3f, 0x1.c71c72p-3f);
+  p = __fmaf_rn(z, p, 0x1.24924ap-2f);
+  p = __fmaf_rn(z, p, 0x1.99999ap-2f);
+  p = __fmaf_rn(z, p, 0x1.555556p-1f);
+  const float r = __fmaf_rn(__fmul_rn(s, z), p, __fmul_rn(2.0f, s));
+  const float ef = __int2float_rn(e);
+  return __fmaf_rn(ef, 0x1.62e4p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, r));
+}
+__device__ __forceinline__ float bm_cos2pi(uint32_t k) {
+  const uint32_t q = (k + (1u << 21)) >> 22;
+  const int ri = (int)k - (int)(q << 22);
+  const float x = __fmul_rn(__fmul_rn(__int2float_rn(ri), 0x1p-24f), 0x1.921fb6p+2f);
+  const float x2 = __fmul_rn(x, x);
+  float c = __fmaf_rn(x2, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);
+  c = __fmaf_rn(x2, c, -0x1.6c16c2p-10f);
+  c = __fmaf_rn(x2, c, 0x1.555556p-5f);
+  c = __fmaf_rn(x2, c, -0.5f);
+  c = __fmaf_rn(x2, c, 1.0f);
+  float sn = __fmaf_rn(x2, 0x1.71de3ap-19f, -0x1.a01a02p-13f);
+  sn = __fmaf_rn(x2, sn, 0x1.111112p-7f);
+  sn = __fmaf_rn(x2, sn, -0x1.555556p-3f);
+  sn = __fmaf_rn(__fmul_rn(x, x2), sn, x);
+  const uint32_t qq = q & 3u;
+  return qq == 0 ? c : (qq == 1 ? -sn : (qq == 2 ? -c : sn));
+}
 __global__ void k_box_muller(int n, uint64_t key, double* __restrict__ z) {
-  const double two_pi = 6.283185307179586;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double u1 = 1.0 - sm64_unif(key, 2 * (uint64_t)i);
-    const double u2 = sm64_unif(key, 2 * (uint64_t)i + 1);
-    z[i] = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+    const uint32_t k1 = sm64_u24(key, 2 * (uint64_t)i), k2 = sm64_u24(key, 2 * (uint64_t)i + 1);
+    const float u1 = __fsub_rn(1.0f, __fmul_rn(__uint2float_rn(k1), 0x1p-24f));
+    const float t = __fmul_rn(-2.0f, bm_ln(u1));
+    z[i] = (double)__fmul_rn(__fsqrt_rn(t), bm_cos2pi(k2));
   }
 }
 

@@ -234,6 +234,22 @@ def test_random_streams_are_uniform_and_normal():
     assert abs(z.mean()) < 5 / np.sqrt(z.size)
 
 
+def test_box_muller_matches_the_transform_in_double():
+    """The single-precision ln/cos sequences of the Box-Muller rhs agree with libm's double
+    transform of the same 24-bit draws to float accuracy (a wrong quadrant, sign or coefficient
+    would be off by O(1) or O(1e-3))."""
+    n = 100000
+    k = O.unif24(240808262, 2, 1, 2 * n).astype(np.float64)
+    u1 = 1.0 - k[0::2] * 2.0**-24
+    u2 = k[1::2] * 2.0**-24
+    ref = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    z = O.box_muller(240808262, 2, n)
+    err = np.abs(z - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() < 2e-6
+    # the quadrant boundaries and the extreme draws are covered
+    assert (u2 < 1e-4).any() and (np.abs(u2 - 0.25) < 1e-4).any() and (np.abs(u2 - 0.75) < 1e-4).any()
+
+
 def test_poly_degree0_closed_form():
     rng = np.random.default_rng(3)
     M = sp.random(30, 30, density=0.2, random_state=4) + 3 * sp.eye(30)
