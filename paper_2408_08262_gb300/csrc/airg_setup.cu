@@ -1076,11 +1076,26 @@ __global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows,
     int cand[kThreadCap];
     double acc[kThreadCap];
     int u = 0;
-    for (int k = ab; k < ae; ++k) {
-      const int l = g.aci[k];
-      const double a = g.av[k];
-      int qb, qe;
-      spg_brow(g, l, qb, qe);
+    // A entries in batches of kGB: their columns, then their B row ranges, are loaded together
+    for (int k0 = ab; k0 < ae; k0 += kGB) {
+      int lb[kGB];
+      double la[kGB];
+      int qbs[kGB], qes[kGB];
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) {
+        lb[t] = (k0 + t < ae) ? g.aci[k0 + t] : -1;
+        la[t] = (k0 + t < ae) ? g.av[k0 + t] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < kGB; ++t) {
+        qbs[t] = 0;
+        qes[t] = 0;
+        if (lb[t] >= 0) spg_brow(g, lb[t], qbs[t], qes[t]);
+      }
+#pragma unroll
+      for (int e = 0; e < kGB; ++e) {
+      const double a = la[e];
+      const int qb = qbs[e], qe = qes[e];
       for (int q = qb; q < qe; ++q) {
         const int j = g.bci[q];
         const double bv = g.bv[q];
@@ -1094,6 +1109,7 @@ __global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows,
         cand[pos] = j;
         acc[pos] = fma(a, bv, 0.0);
         ++u;
+      }
       }
     }
     long long mx = 0;
