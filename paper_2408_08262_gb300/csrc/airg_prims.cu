@@ -91,6 +91,37 @@ __global__ void k_tile_scan(const T* __restrict__ in, T* __restrict__ out, const
   }
 }
 
+// One CTA scans up to kScanSingle entries in one launch (tiles of 1024 x 8 in sequence, carrying
+// the running offset): on small levels the launch count, not the bandwidth, is what costs.
+constexpr int kScanSingle = 1 << 16;
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_scan_single(const T* __restrict__ in, T* __restrict__ out, int n) {
+  __shared__ T carry, tot;
+  if (threadIdx.x == 0) carry = T(0);
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024 * kScanItems) {
+    const int b0 = base + threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T loc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      v[j] = (b0 + j < n) ? in[b0 + j] : T(0);
+      loc += v[j];
+    }
+    T run = block_excl_scan<T>(loc, &tot) + carry;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      if (b0 + j < n) out[b0 + j] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
 template <class T>
 static int scan_impl(const T* in, T* out, int n, Arena& tmp, cudaStream_t s, long long* total_host) {
   if (n <= 0) {
@@ -100,7 +131,11 @@ static int scan_impl(const T* in, T* out, int n, Arena& tmp, cudaStream_t s, lon
   }
   int nt = ceil_div(n, kScanTile);
   T* toff = nullptr;
-  if (nt > 1) {
+  if (nt > 1 && n <= kScanSingle) {
+    airg::note_launch(), k_scan_single<T><<<1, 1024, 0, s>>>(in, out, n);
+    KERNEL_CHECK();
+    nt = 0;
+  } else if (nt > 1) {
     T* tsum = nullptr;
     AIRG_TRY(tmp.alloc(&tsum, nt));
     AIRG_TRY(tmp.alloc(&toff, (size_t)nt + 1));
@@ -108,8 +143,10 @@ static int scan_impl(const T* in, T* out, int n, Arena& tmp, cudaStream_t s, lon
     KERNEL_CHECK();
     AIRG_TRY(scan_impl<T>(tsum, toff, nt, tmp, s, nullptr));
   }
-  airg::note_launch(), k_tile_scan<T><<<nt, kScanThreads, 0, s>>>(in, out, toff, n);
-  KERNEL_CHECK();
+  if (nt > 0) {
+    airg::note_launch(), k_tile_scan<T><<<nt, kScanThreads, 0, s>>>(in, out, toff, n);
+    KERNEL_CHECK();
+  }
   if (total_host) {
     T t = 0;
     CU_TRY(cudaMemcpyAsync(&t, out + n, sizeof(T), cudaMemcpyDeviceToHost, s));

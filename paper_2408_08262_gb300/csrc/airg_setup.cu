@@ -333,6 +333,51 @@ __global__ void k_radix_pick(RadixState* st, int shift, unsigned* hist) {
   for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
 }
 
+// The eight passes of the radix select in one CTA (small levels: one launch instead of sixteen);
+// the digit rule is k_radix_pick's.
+__global__ void __launch_bounds__(1024) k_radix_single(int n, const int8_t* __restrict__ cf,
+                                                       const double* __restrict__ theta, RadixState* st) {
+  __shared__ unsigned sh[256];
+  __shared__ unsigned long long prefix, mask;
+  __shared__ long long krem;
+  if (st->k <= 0) return;
+  if (threadIdx.x == 0) {
+    prefix = st->prefix;
+    mask = st->mask;
+    krem = st->krem;
+  }
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) sh[t] = 0;
+    __syncthreads();
+    const unsigned long long pf = prefix, mk = mask;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(theta[i]);
+      if (cf[i] != kF || bits == 0ULL) continue;
+      if ((bits & mk) == pf) atomicAdd(&sh[(bits >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long cum = 0;
+      int d = 0;
+      for (d = 255; d >= 0; --d) {
+        if (cum + (long long)sh[d] >= krem) break;
+        cum += sh[d];
+      }
+      if (d < 0) d = 0;
+      krem -= cum;
+      prefix |= ((unsigned long long)d) << shift;
+      mask |= 255ULL << shift;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->prefix = prefix;
+    st->mask = mask;
+    st->krem = krem;
+  }
+}
+
 __global__ void k_ddc_apply(int n, int8_t* __restrict__ cf, const double* __restrict__ theta, const RadixState* st,
                             int* converted) {
   if (st->k <= 0) return;
@@ -400,10 +445,14 @@ int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t
   AIRG_TRY(tmp.alloc(&hist, 256));
   CU_TRY(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned), s));
   airg::note_launch(), k_ddc_init<<<1, 32, 0, s>>>(ctr, p.ddc_fraction, st);
-  for (int pass = 0; pass < 8; ++pass) {
-    const int shift = 56 - 8 * pass;
-    airg::note_launch(), k_radix_hist<<<GRID(n)>>>(n, cf, theta, st, shift, hist);
-    airg::note_launch(), k_radix_pick<<<1, 256, 0, s>>>(st, shift, hist);
+  if (n <= 65536) {
+    airg::note_launch(), k_radix_single<<<1, 1024, 0, s>>>(n, cf, theta, st);
+  } else {
+    for (int pass = 0; pass < 8; ++pass) {
+      const int shift = 56 - 8 * pass;
+      airg::note_launch(), k_radix_hist<<<GRID(n)>>>(n, cf, theta, st, shift, hist);
+      airg::note_launch(), k_radix_pick<<<1, 256, 0, s>>>(st, shift, hist);
+    }
   }
   airg::note_launch(), k_ddc_apply<<<GRID(n)>>>(n, cf, theta, st, ctr + 2);
   KERNEL_CHECK();
