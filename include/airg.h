@@ -66,9 +66,9 @@ typedef struct {
  * (Section "Parallel results"): strength 0.5, n_loops^max = 3, DDC fraction 10 %, drop 0.01 on Z
  * and 0.001 on the coarse matrices, 6th-order polynomials (m = 7) with first-order fixed sparsity; two up F-smooths (Section "Results"); the coarse solve uses
  * three iterations of a 12th-order fixed-sparsity polynomial (Section "Timing results"), with the
- * hierarchy truncated automatically at clamp(n_top / 16, 64, 30000) unknowns (the paper truncates
- * at ~300k on CPU ranks; 30k is where one GB300 is fastest on the 6.29M-DOF benchmark system with
- * unchanged iteration counts, and smaller systems keep a multilevel hierarchy). */
+ * hierarchy truncated automatically at clamp(n_top / 16, 64, 60000) unknowns (the paper truncates
+ * at ~300k on CPU ranks; on one GB300, setup plus solve time averaged over seeds is lowest near 60k
+ * for the 1.57M- and 6.29M-DOF systems, and smaller systems keep a multilevel hierarchy). */
 typedef struct {
   double strong_threshold;  /* alpha in eq. soc, in [0, 1] */
   double ddc_fraction;      /* fraction of F-points DDC converts, in [0, 1] */
@@ -77,7 +77,7 @@ typedef struct {
   int coarse_poly_order;    /* degree of the coarsest-level polynomial */
   int coarse_iters;         /* iterations of the coarsest-level polynomial solve (>= 1) */
   int coarse_size;          /* a level with n <= coarse_size is the coarsest; <= 0: automatic,
-                               clamp(n_top / 16, 64, 30000) */
+                               clamp(n_top / 16, 64, 60000) */
   int max_levels;           /* hierarchy depth cap (>= 1) */
   double drop_R;            /* relative row-wise inf-norm drop on Z */
   double drop_Ac;           /* relative row-wise inf-norm drop on A_c (diagonal always kept) */

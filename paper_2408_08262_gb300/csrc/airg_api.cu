@@ -81,7 +81,7 @@ double avg_len(const DCsr& A) { return A.nrows > 0 ? (double)A.nnz / A.nrows : 1
 int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   cudaStream_t s = H->s;
   SetupParams sp = to_setup(H->p);
-  if (sp.coarse_size <= 0) sp.coarse_size = (int)std::min<long long>(30000, std::max<long long>(64, (long long)Ain->n / 16));
+  if (sp.coarse_size <= 0) sp.coarse_size = (int)std::min<long long>(60000, std::max<long long>(64, (long long)Ain->n / 16));
   Arena tmp;
   tmp.s = s;
   struct Rel {
