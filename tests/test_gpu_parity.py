@@ -268,6 +268,29 @@ def test_solve_is_deterministic():
     assert torch.equal(x1, x2)
 
 
+def test_setup_is_deterministic_run_to_run():
+    """Two independent setups of one matrix give bitwise-identical hierarchies: the TSQR combine
+    order, the SpGEMM accumulation order and every reduction are fixed, whatever order the warps,
+    the atomics and the two streams run in."""
+    p = P.blocked_sigma_2d(256)
+    par = airg.Params(keep_setup=1)
+    H1 = airg.Hierarchy(*dev(p), par)
+    H2 = airg.Hierarchy(*dev(p), par)
+    assert H1.num_levels == H2.num_levels
+    for l in range(H1.num_levels):
+        v1, v2 = H1.vectors(l), H2.vectors(l)
+        assert np.array_equal(v1["alpha"], v2["alpha"]), l
+        assert np.array_equal(v1["cf"], v2["cf"]) and np.array_equal(v1["w"], v2["w"]), l
+        names = ["A", "Ainv"] if H1.level_info(l)["coarsest"] else ["A", "Ainv", "Z", "AF_solve", "Z_solve"]
+        for which in names:
+            for a, b in zip(H1.export(l, which), H2.export(l, which)):
+                assert np.array_equal(a, b), (l, which)
+    b = torch.from_numpy(p.b).cuda()
+    x1, i1 = H1.solve(b, rtol=1e-10)
+    x2, i2 = H2.solve(b, rtol=1e-10)
+    assert i1 == i2 and torch.equal(x1, x2)
+
+
 def test_graph_and_eager_vcycles_agree_bitwise(monkeypatch):
     p = P.blocked_sigma_2d(80)
     b = torch.from_numpy(p.b).cuda()
@@ -353,6 +376,18 @@ def test_full_size_cf_split_bitexact(big):
     ref = O.cf_split(big.rowptr, big.col, big.val, op)["cf"]
     got = airg.cf_split(*dev(big), gpu_params(op), level=0).cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+def test_full_size_setup_is_deterministic(big):
+    b = torch.from_numpy(big.b).cuda()
+    xs = []
+    for _ in range(2):
+        H = airg.Hierarchy(*dev(big), airg.Params())
+        x, info = H.solve(b, rtol=1e-8)
+        xs.append((x, info["iters"], H.num_levels))
+        H.close()
+    assert xs[0][1:] == xs[1][1:]
+    assert torch.equal(xs[0][0], xs[1][0])
 
 
 def test_full_size_solve_reaches_tolerance(big):
