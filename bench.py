@@ -335,6 +335,27 @@ def main():
                        "iters": max(its), "relres": inf["relres"], "dofs_per_s": p.n / (ms / 1e3),
                        "solve_speedup_vs_fp64": round(min(solve_ms) / min(so), 3)}
 
+    # parameter variant the paper sweeps: GMRES-polynomial order 1..6 with first-order fixed sparsity
+    # (the paper's table of orders 1-6), same system, setup and solve to the same rtol
+    poly_sweep = None
+    if not args.no_forms:
+        poly_sweep = {}
+        for d in range(1, 7):
+            par = airg.Params(poly_order=d)
+            Hw = airg.Hierarchy(rp, ci, v, par)
+            Hw.solve(b, rtol=args.rtol, restart=args.restart)
+            Hw.close()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            Hd = airg.Hierarchy(rp, ci, v, par)
+            t1 = time.perf_counter()
+            xd, ind = Hd.solve(b, rtol=args.rtol, restart=args.restart)
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+            Hd.close()
+            poly_sweep[str(d)] = {"setup_ms": round(1e3 * (t1 - t0), 2), "solve_ms": round(1e3 * (t2 - t1), 2),
+                                  "iters": ind["iters"], "status": ind["status"]}
+
     # batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle graph,
     # against the same 64 systems solved one after another (same hierarchies)
     batched, adjoint = None, None
@@ -429,7 +450,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "mixed_precision_forms": forms,
-                "batched_form": batched, "adjoint_form": adjoint,
+                "batched_form": batched, "adjoint_form": adjoint, "poly_order_sweep": poly_sweep,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

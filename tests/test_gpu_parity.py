@@ -192,6 +192,26 @@ def test_vcycle_matches_oracle_two_levels():
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-12
 
 
+def test_ideal_operators_two_level_exact_on_gpu():
+    """Section "Reduction multigrid", eq. prolong: with exact A_ff^-1 (unit diagonal and strength 0
+    make A_ff = I, so the degree-0 polynomial is exact), no drops and a converged coarse solve,
+    R A P is the Schur complement and one V-cycle solves exactly."""
+    import scipy.sparse as sps
+    p = P.streaming_2d(4)
+    A = p.scipy()
+    d = 1.0 / A.diagonal()
+    As = sps.csr_matrix(sps.diags(d) @ A)
+    As.sort_indices()
+    b = d * p.b
+    op = O.Params(strong_threshold=0.0, ddc_fraction=0.0, drop_R=0.0, drop_Ac=0.0, poly_order=0,
+                  max_levels=2, coarse_size=1, coarse_poly_order=8, coarse_iters=200, n_smooth_up=1)
+    H = airg.Hierarchy(*dev((As.indptr.astype(np.int32), As.indices.astype(np.int32), As.data)), gpu_params(op))
+    assert H.num_levels == 2
+    x = H.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    xs = np.linalg.solve(As.toarray(), b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-12
+
+
 @pytest.mark.parametrize("mesh,gen", [(40, "2d"), (64, "2d"), (12, "3d")])
 def test_deep_vcycle_applies_its_operators_exactly(mesh, gen):
     p = P.streaming_2d(mesh) if gen == "2d" else P.kuhn_3d(mesh)
@@ -216,7 +236,7 @@ def solve_both(p, op, outer="fgmres", rtol=1e-12, max_it=300):
     return xo, io, xg.cpu().numpy(), ig, Hg
 
 
-@pytest.mark.parametrize("mesh,degree", [(64, 2), (64, 6), (33, 6), (128, 6)])
+@pytest.mark.parametrize("mesh,degree", [(64, 2), (64, 6), (33, 6), (128, 6), (48, 1), (48, 3), (48, 4), (48, 5)])
 def test_solution_matches_oracle(mesh, degree):
     # (64, 2) is the 24,576-DOF pure-streaming configuration with a degree-2 polynomial
     p = P.streaming_2d(mesh)
@@ -225,6 +245,22 @@ def test_solution_matches_oracle(mesh, degree):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
     assert abs(ig["iters"] - io["iters"]) <= 1
     assert ig["relres"] <= 1e-12
+
+
+def test_polynomial_order_trend():
+    """Section "Parallel results" (GMRES-polynomial table): with first-order fixed sparsity the
+    iteration count falls steeply from order 1 and flattens by order 4-6."""
+    p = P.blocked_sigma_2d(256)
+    b = torch.from_numpy(p.b).cuda()
+    its = []
+    for d in range(1, 7):
+        H = airg.Hierarchy(*dev(p), airg.Params(poly_order=d))
+        x, info = H.solve(b, rtol=1e-10, max_it=2000)
+        assert info["status"] == 0, (d, info)
+        its.append(info["iters"])
+        H.close()
+    assert its[0] >= 2 * its[5], its
+    assert all(its[k + 1] <= its[k] + 1 for k in range(5)), its
 
 
 def test_richardson_matches_oracle():
