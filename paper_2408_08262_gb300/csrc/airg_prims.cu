@@ -345,6 +345,17 @@ template <>
 __device__ __forceinline__ float vt_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename VT, typename XT>
+__device__ __forceinline__ XT vfma(VT a, XT x, XT acc);
+template <>
+__device__ __forceinline__ double vfma<double, double>(double a, double x, double acc) { return fma(a, x, acc); }
+template <>
+__device__ __forceinline__ float vfma<float, float>(float a, float x, float acc) { return fmaf(a, x, acc); }
+template <>
+__device__ __forceinline__ float vfma<__nv_bfloat16, float>(__nv_bfloat16 a, float x, float acc) {
+  return fmaf(__bfloat162float(a), x, acc);
+}
+
+template <typename VT, typename XT>
 __device__ __forceinline__ XT vmul(VT a, XT x);
 template <>
 __device__ __forceinline__ double vmul<double, double>(double a, double x) { return a * x; }
@@ -409,9 +420,72 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
   }
 }
 
+// Short rows (average <= 12 entries): one thread per row reads its own entries directly (the
+// warp's rows are contiguous, so the lines they touch arrive once in L1) and accumulates with one
+// fused multiply-add per entry, in storage order; no shared memory and no barrier.
+template <typename VT, typename XT, int MODE, bool PROLONG>
+__global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                  const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
+                                                  const int* __restrict__ w, XT* xf) {
+  for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < nrows; rr += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)rr;
+    const int rb = rp[row], re = rp[row + 1];
+    XT s = XT(0);
+    for (int k0 = rb; k0 < re; k0 += 4) {
+      int c[4];
+      VT a[4];
+      XT xv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        c[t] = (k0 + t < re) ? __ldcs(ci + k0 + t) : -1;
+        a[t] = (k0 + t < re) ? __ldcs(v + k0 + t) : VT(0);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        xv[t] = XT(0);
+        if (c[t] >= 0) {
+          if (PROLONG && c[t] < nrows) {
+            const int src = w[c[t]];
+            xv[t] = src >= 0 ? x[nrows + src] : XT(0);
+          } else {
+            xv[t] = __ldg(x + c[t]);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
+    }
+    XT out;
+    if (MODE == SPMV_SET) out = s;
+    else if (MODE == SPMV_RESID) out = b[row] - s;
+    else if (MODE == SPMV_ADD) out = y[row] + s;
+    else out = b[row] + s;
+    y[row] = out;
+    if (PROLONG) {
+      const int src = w[row];
+      xf[row] = src >= 0 ? x[nrows + src] : XT(0);
+    }
+  }
+}
+
 template <typename VT, typename XT, int LPR>
 static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
                         const int* w, XT* xf, cudaStream_t s) {
+  if (LPR == 1) {
+    const int g1 = ceil_div(nrows, 256);
+    if (w) {
+      airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
+      return;
+    }
+    switch (mode) {
+      case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+      case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+      case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+      default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    }
+    return;
+  }
   const int grid = ceil_div(nrows, kSpmvThreads / LPR);
   if (w) {
     airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
