@@ -420,10 +420,11 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __r
   }
 }
 
-// Short rows (average <= 12 entries): one thread per row reads its own entries directly (the
+// Short rows (average <= 12 entries): one thread per row reads its own entries directly, kRowBatch
+// (4 for rows of about 4 entries or fewer, else 8) at a time (the
 // warp's rows are contiguous, so the lines they touch arrive once in L1) and accumulates with one
 // fused multiply-add per entry, in storage order; no shared memory and no barrier.
-template <typename VT, typename XT, int MODE, bool PROLONG>
+template <typename VT, typename XT, int MODE, bool PROLONG, int kRowBatch>
 __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
                                                   const int* __restrict__ w, XT* xf) {
@@ -431,17 +432,17 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
     const int row = (int)rr;
     const int rb = rp[row], re = rp[row + 1];
     XT s = XT(0);
-    for (int k0 = rb; k0 < re; k0 += 4) {
-      int c[4];
-      VT a[4];
-      XT xv[4];
+    for (int k0 = rb; k0 < re; k0 += kRowBatch) {
+      int c[kRowBatch];
+      VT a[kRowBatch];
+      XT xv[kRowBatch];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < kRowBatch; ++t) {
         c[t] = (k0 + t < re) ? __ldcs(ci + k0 + t) : -1;
         a[t] = (k0 + t < re) ? __ldcs(v + k0 + t) : VT(0);
       }
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < kRowBatch; ++t) {
         xv[t] = XT(0);
         if (c[t] >= 0) {
           if (PROLONG && c[t] < nrows) {
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
         }
       }
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
+      for (int t = 0; t < kRowBatch; ++t)
         if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
     }
     XT out;
@@ -469,21 +470,28 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
   }
 }
 
+template <typename VT, typename XT, int RB>
+static void launch_spmv_row(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y,
+                            int mode, const int* w, XT* xf, cudaStream_t s) {
+  const int g1 = ceil_div(nrows, 256);
+  if (w) {
+    airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
+    return;
+  }
+  switch (mode) {
+    case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+  }
+}
+
 template <typename VT, typename XT, int LPR>
 static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                        const int* w, XT* xf, cudaStream_t s) {
-  if (LPR == 1) {
-    const int g1 = ceil_div(nrows, 256);
-    if (w) {
-      airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
-      return;
-    }
-    switch (mode) {
-      case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-      case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-      case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-      default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    }
+                        const int* w, XT* xf, cudaStream_t s, int rb) {
+  if constexpr (LPR == 1) {
+    if (rb == 8) launch_spmv_row<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s);
+    else launch_spmv_row<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s);
     return;
   }
   const int grid = ceil_div(nrows, kSpmvThreads / LPR);
@@ -501,20 +509,23 @@ static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, co
 
 template <typename VT, typename XT>
 static void spmv_dispatch(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                          int lanes, const int* w, XT* xf, cudaStream_t s) {
+                          int lanes, const int* w, XT* xf, cudaStream_t s, int rb) {
   switch (lanes) {
-    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
-    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
-    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
-    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
-    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
-    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s); break;
+    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
   }
 }
 
+// Entries loaded per batch by the row-per-thread SpMV: 8 unless the rows average about 4 or fewer.
+static int row_batch(const DCsr& A) { return (double)A.nnz > 4.5 * (double)A.nrows ? 8 : 4; }
+
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
-  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s);
+  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s, row_batch(A));
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -523,7 +534,7 @@ int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mod
 int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
                            cudaStream_t s) {
   if (AF.nrows <= 0) return AIRG_OK;
-  spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s);
+  spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s, row_batch(AF));
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -535,9 +546,10 @@ int dev_spmv_lo(const DCsr& A, const void* vals, int vt, const float* x, const f
   if (A.nrows <= 0) return AIRG_OK;
   float* xf = w ? const_cast<float*>(x) : nullptr;
   if (vt == 2)
-    spmv_dispatch<__nv_bfloat16, float>(A.nrows, A.rp, A.ci, (const __nv_bfloat16*)vals, x, b, y, mode, lanes, w, xf, s);
+    spmv_dispatch<__nv_bfloat16, float>(A.nrows, A.rp, A.ci, (const __nv_bfloat16*)vals, x, b, y, mode, lanes, w, xf, s,
+                                        row_batch(A));
   else
-    spmv_dispatch<float, float>(A.nrows, A.rp, A.ci, (const float*)vals, x, b, y, mode, lanes, w, xf, s);
+    spmv_dispatch<float, float>(A.nrows, A.rp, A.ci, (const float*)vals, x, b, y, mode, lanes, w, xf, s, row_batch(A));
   KERNEL_CHECK();
   return AIRG_OK;
 }
