@@ -14,37 +14,6 @@ using namespace airg;
 namespace airg {
 std::atomic<long long> g_launches{0};
 
-namespace {
-std::mutex g_pool_mu;
-cudaMemPool_t g_pool[256] = {};
-bool g_pool_tried[256] = {};
-}  // namespace
-
-// Up to 16 GiB of freed chunks stay cached in the pool between setups.
-cudaMemPool_t library_pool() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  std::lock_guard<std::mutex> lk(g_pool_mu);
-  if (!g_pool_tried[dev]) {
-    g_pool_tried[dev] = true;
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.handleTypes = cudaMemHandleTypeNone;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t pool = nullptr;
-    if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
-      uint64_t keep = (uint64_t)16 << 30;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-      g_pool[dev] = pool;
-    }
-    cudaGetLastError();
-  }
-  return g_pool[dev];
-}
 }
 
 namespace {

@@ -40,14 +40,8 @@ struct DCsr {
   double* v = nullptr;
 };
 
-// The library's stream-ordered memory pool on the current device (created on first use): freed
-// chunks stay cached in it, up to a release threshold, so that a new setup does not go back to the
-// driver for memory a previous one returned.  nullptr if no pool could be made (the device's
-// default pool is used then).
-cudaMemPool_t library_pool();
-
 // Stream-ordered device memory.  An Arena hands out 256-byte-aligned sub-ranges of large chunks
-// obtained from library_pool() (bump allocation), so a hierarchy owns a handful of blocks rather
+// obtained with cudaMallocAsync (bump allocation), so a hierarchy owns a handful of blocks rather
 // than thousands of arrays.  reset() makes every chunk reusable (all users are on the same stream,
 // so later kernels see the memory only after earlier ones are done); release() frees the chunks.
 struct Arena {
@@ -76,8 +70,7 @@ struct Arena {
     if (no_grow) return AIRG_ERR_SCRATCH;
     size_t sz = bytes > chunk_min ? bytes : chunk_min;
     void* b = nullptr;
-    cudaMemPool_t pool = library_pool();
-    cudaError_t e = pool ? cudaMallocFromPoolAsync(&b, sz, pool, s) : cudaMallocAsync(&b, sz, s);
+    cudaError_t e = cudaMallocAsync(&b, sz, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e == cudaErrorMemoryAllocation ? AIRG_ERR_OOM : AIRG_ERR_CUDA;
