@@ -54,16 +54,16 @@ def spmv_traffic():
     """DRAM bytes per top-level SpMV launch from the committed ncu summary, or None when the kernel
     source has changed since that capture (the summary records a hash of the kernel's source)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_spmv_top_level_2d_p1dg_640.md")
+    prof = os.path.join(ROOT, "profiles", "k_spmv_row_top_level_2d_p1dg_640.md")
     src = os.path.join(ROOT, "paper_2408_08262_gb300", "csrc", "airg_prims.cu")
     try:
         txt = open(prof).read()
         code = open(src).read()
-        a = code.index("__global__ void __launch_bounds__(kSpmvThreads) k_spmv(")
+        a = code.index("__global__ void __launch_bounds__(256) k_spmv_row(")
         b = code.index("\n}\n", a) + 3
         h = hashlib.sha256(code[a:b].encode()).hexdigest()[:16]
         vals = dict(line.split(": ", 1) for line in txt.splitlines() if ": " in line and line.split(": ")[0].strip().isidentifier())
-        if vals.get("k_spmv_source_sha256_16", "").strip() != h:
+        if vals.get("k_spmv_row_source_sha256_16", "").strip() != h:
             return None
         return float(vals["traffic_bytes_per_launch_1024"])
     except Exception:
@@ -224,7 +224,8 @@ def main():
     info0, kt0, lv0 = step(profile=True)
     for _ in range(max(0, args.warmup - 1)):
         step()
-    # The roofline kernel is the tiled CSR SpMV (k_spmv), the dominant kernel of the step.  In the
+    # The roofline kernel is the CSR SpMV (k_spmv_row on the short-row operators, the tiled k_spmv
+    # on long rows), the dominant kernel family of the step.  In the
     # timed region its top-level-operator launches (the largest instance, 6.29M rows) are timed
     # with CUDA events; timing every small-level launch inside the V-cycle graph would itself slow
     # the solve.  The warm-up step times every class and is reported in config.
@@ -297,7 +298,7 @@ def main():
     per_launch_bytes = dom["bytes"] / max(1, dom["launches"])
     fam_bytes = sum(kt0[c]["bytes"] for c in all_spmv)
     fam_ms = sum(kt0[c]["ms"] for c in all_spmv)
-    roofline = {"bound": "hbm", "kernel": "k_spmv, top-level operator launches (A z in FGMRES, 6.29M rows)",
+    roofline = {"bound": "hbm", "kernel": "k_spmv_row (row-per-thread CSR SpMV), top-level operator launches (A z in FGMRES, 6.29M rows)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                 "traffic": (spmv_traffic() if args.mesh == 1024 else None), "algorithmic_bytes_per_launch": per_launch_bytes,
