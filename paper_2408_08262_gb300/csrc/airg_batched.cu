@@ -61,44 +61,48 @@ __global__ void k_gather_map(const double* __restrict__ x, const int* __restrict
     y[r] = x[map[r]];
 }
 
-// Tiled SpMV (same scheme as the single-system kernel) with a row map:
+// SpMV with a row map (same scheme as the single-system kernels: the LPR lanes of a row read its
+// entries directly, 4 per batch, accumulate with FMAs and combine by a butterfly):
 //   SET: y[map r] = s;  RESID: y[r] = b[map r] - s;  ADD: y[map r] += s;  ADDB: y[map r] = b[map r] + s
 template <int LPR, int MODE>
 __global__ void __launch_bounds__(256) k_spmv_mapped(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const double* __restrict__ v, const double* x, const double* b,
                                                      double* y, const int* __restrict__ map) {
-  constexpr int RPB = 256 / LPR;
-  __shared__ double prod[2048];
-  const int r0 = blockIdx.x * RPB;
-  const int r1 = min(r0 + RPB, nrows);
-  const int lane = threadIdx.x % LPR;
-  const int row = r0 + threadIdx.x / LPR;
-  const bool has = row < r1;
-  const int rb = has ? rp[row] : 0;
-  const int re = has ? rp[row + 1] : 0;
-  const int k0 = rp[r0], k1 = rp[r1];
-  double s = 0.0;
-  for (int c0 = k0; c0 < k1; c0 += 2048) {
-    const int c1 = min(c0 + 2048, k1);
-#pragma unroll 4
-    for (int k = c0 + threadIdx.x; k < c1; k += 256) prod[k - c0] = __ldcs(v + k) * x[__ldcs(ci + k)];
-    __syncthreads();
-    if (has) {
-      const int lo = max(rb, c0), hi = min(re, c1);
-      for (int k = lo + lane; k < hi; k += LPR) s += prod[k - c0];
+  constexpr int GPW = 32 / LPR;
+  const int lane = threadIdx.x % LPR, grp = (threadIdx.x & 31) / LPR;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * GPW; base < nrows; base += nwarps * GPW) {  // warp-uniform
+    const long long rr = base + grp;
+    const bool act = rr < nrows;
+    const int row = act ? (int)rr : 0;
+    const int rb = act ? rp[row] : 0, re = act ? rp[row + 1] : 0;
+    double s = 0.0;
+    for (int k0 = rb + lane; k0 < re; k0 += 4 * LPR) {
+      int c[4];
+      double a[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = k0 + t * LPR;
+        c[t] = (k < re) ? __ldcs(ci + k) : -1;
+        a[t] = (k < re) ? __ldcs(v + k) : 0.0;
+      }
+      double xv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) xv[t] = (c[t] >= 0) ? __ldg(x + c[t]) : 0.0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c[t] >= 0) s = fma(a[t], xv[t], s);
     }
-    __syncthreads();
-  }
-  if (LPR > 1) {
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-  }
-  if (has && lane == 0) {
-    const int m = map[row];
-    if (MODE == SPMV_SET) y[m] = s;
-    else if (MODE == SPMV_RESID) y[row] = b[m] - s;
-    else if (MODE == SPMV_ADD) y[m] = y[m] + s;
-    else y[m] = b[m] + s;
+    if (act && lane == 0) {
+      const int m = map[row];
+      if (MODE == SPMV_SET) y[m] = s;
+      else if (MODE == SPMV_RESID) y[row] = b[m] - s;
+      else if (MODE == SPMV_ADD) y[m] = y[m] + s;
+      else y[m] = b[m] + s;
+    }
   }
 }
 

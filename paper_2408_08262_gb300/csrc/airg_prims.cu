@@ -324,25 +324,14 @@ int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, d
 }
 
 // ------------------------------------------------------------------------------------------
-// CSR SpMV, tiled: a CTA owns 256 consecutive rows.  Their nonzeros (a contiguous range of the CSR
-// arrays) are streamed in chunks of kSpmvChunk entries with coalesced loads of values and column
-// indices and independent gathers of x; the products go to shared memory and each thread then sums
-// its own row's products in ascending column-storage order (the plain sequential row sum).  All
-// loads of a chunk are independent of one another, so many are in flight per thread, which is what
-// a 5-nonzeros-per-row matrix needs to approach the HBM roofline.
-// ------------------------------------------------------------------------------------------
-constexpr int kSpmvThreads = 256;
-constexpr int kSpmvChunk = 2048;
-
-// LPR lanes sum each row (LPR = 1: one thread per row, summing in storage order); a CTA owns
-// kSpmvThreads / LPR consecutive rows, so operators with long rows still give many CTAs.
-// PROLONG: first F-smoothing residual with the one-point prolongation fused in (see
+// CSR SpMV.  Every kernel reads the rows' entries directly (columns and values streamed with
+// evict-first loads, so that x stays in L2), gathers x and accumulates with one fused multiply-add
+// per entry: one thread per row for short rows (k_spmv_row), LPR lanes per row for longer ones
+// (k_spmv_vec).  PROLONG: first F-smoothing residual with the one-point prolongation fused in (see
 // dev_spmv_resid_prolong).  VT is the stored value type (double, float or bf16), XT the vector and
 // accumulation type (double for the FP64 path, float for the mixed-precision V-cycle).
-template <typename VT>
-__device__ __forceinline__ float vt_to_f(VT v) { return (float)v; }
-template <>
-__device__ __forceinline__ float vt_to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+// ------------------------------------------------------------------------------------------
+constexpr int kSpmvThreads = 256;
 
 template <typename VT, typename XT>
 __device__ __forceinline__ XT vfma(VT a, XT x, XT acc);
@@ -355,70 +344,7 @@ __device__ __forceinline__ float vfma<__nv_bfloat16, float>(__nv_bfloat16 a, flo
   return fmaf(__bfloat162float(a), x, acc);
 }
 
-template <typename VT, typename XT>
-__device__ __forceinline__ XT vmul(VT a, XT x);
-template <>
-__device__ __forceinline__ double vmul<double, double>(double a, double x) { return a * x; }
-template <>
-__device__ __forceinline__ float vmul<float, float>(float a, float x) { return a * x; }
-template <>
-__device__ __forceinline__ float vmul<__nv_bfloat16, float>(__nv_bfloat16 a, float x) { return __bfloat162float(a) * x; }
 
-template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmv(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                       const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
-                                                       const int* __restrict__ w, XT* xf) {
-  constexpr int RPB = kSpmvThreads / LPR;
-  constexpr int CHUNK = kSpmvChunk * (int)(sizeof(double) / sizeof(XT));
-  __shared__ XT prod[CHUNK];
-  const int r0 = blockIdx.x * RPB;
-  const int r1 = min(r0 + RPB, nrows);
-  const int lane = threadIdx.x % LPR;
-  const int row = r0 + threadIdx.x / LPR;
-  const bool has = row < r1;
-  const int rb = has ? rp[row] : 0;
-  const int re = has ? rp[row + 1] : 0;
-  const int k0 = rp[r0], k1 = rp[r1];
-  XT s = XT(0);
-  for (int c0 = k0; c0 < k1; c0 += CHUNK) {
-    const int c1 = min(c0 + CHUNK, k1);
-    // matrix values and columns are read once: stream them (evict-first) so that x stays in L2
-#pragma unroll 4
-    for (int k = c0 + threadIdx.x; k < c1; k += kSpmvThreads) {
-      const int c = __ldcs(ci + k);
-      XT xv;
-      if (PROLONG && c < nrows) {
-        const int src = w[c];
-        xv = src >= 0 ? x[nrows + src] : XT(0);
-      } else {
-        xv = __ldg(x + c);
-      }
-      prod[k - c0] = vmul<VT, XT>(__ldcs(v + k), xv);
-    }
-    __syncthreads();
-    if (has) {
-      const int lo = max(rb, c0), hi = min(re, c1);
-      for (int k = lo + lane; k < hi; k += LPR) s += prod[k - c0];
-    }
-    __syncthreads();
-  }
-  if (LPR > 1) {
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-  }
-  if (has && lane == 0) {
-    XT out;
-    if (MODE == SPMV_SET) out = s;
-    else if (MODE == SPMV_RESID) out = b[row] - s;
-    else if (MODE == SPMV_ADD) out = y[row] + s;
-    else out = b[row] + s;
-    y[row] = out;
-    if (PROLONG) {
-      const int src = w[row];
-      xf[row] = src >= 0 ? x[nrows + src] : XT(0);
-    }
-  }
-}
 
 // Short rows (average <= 12 entries): one thread per row reads its own entries directly, kRowBatch
 // (4 for rows of about 4 entries or fewer, else 8) at a time (the
@@ -470,6 +396,67 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
   }
 }
 
+// Longer rows (LPR = 2..32 lanes per row): the LPR lanes of a row read its entries directly,
+// lane l taking entries l, l + LPR, ... (4 per batch), accumulate with FMAs and combine by a
+// butterfly over the LPR lanes.  No shared memory and no barrier.
+template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
+__global__ void __launch_bounds__(256) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                  const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
+                                                  const int* __restrict__ w, XT* xf) {
+  constexpr int GPW = 32 / LPR;  // rows per warp and pass
+  const int lane = threadIdx.x % LPR, grp = (threadIdx.x & 31) / LPR;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  // warp-uniform loop, so that every lane reaches the butterfly below
+  for (long long base = warp * GPW; base < nrows; base += nwarps * GPW) {
+    const long long rr = base + grp;
+    const bool act = rr < nrows;
+    const int row = act ? (int)rr : 0;
+    const int rb = act ? rp[row] : 0, re = act ? rp[row + 1] : 0;
+    XT s = XT(0);
+    for (int k0 = rb + lane; k0 < re; k0 += 4 * LPR) {
+      int c[4];
+      VT a[4];
+      XT xv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = k0 + t * LPR;
+        c[t] = (k < re) ? __ldcs(ci + k) : -1;
+        a[t] = (k < re) ? __ldcs(v + k) : VT(0);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        xv[t] = XT(0);
+        if (c[t] >= 0) {
+          if (PROLONG && c[t] < nrows) {
+            const int src = w[c[t]];
+            xv[t] = src >= 0 ? x[nrows + src] : XT(0);
+          } else {
+            xv[t] = __ldg(x + c[t]);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
+    if (act && lane == 0) {
+      XT out;
+      if (MODE == SPMV_SET) out = s;
+      else if (MODE == SPMV_RESID) out = b[row] - s;
+      else if (MODE == SPMV_ADD) out = y[row] + s;
+      else out = b[row] + s;
+      y[row] = out;
+      if (PROLONG) {
+        const int src = w[row];
+        xf[row] = src >= 0 ? x[nrows + src] : XT(0);
+      }
+    }
+  }
+}
+
 template <typename VT, typename XT, int RB>
 static void launch_spmv_row(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y,
                             int mode, const int* w, XT* xf, cudaStream_t s) {
@@ -496,14 +483,14 @@ static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, co
   }
   const int grid = ceil_div(nrows, kSpmvThreads / LPR);
   if (w) {
-    airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
+    airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    default: airg::note_launch(), k_spmv<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_SET: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    default: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
   }
 }
 
