@@ -224,8 +224,8 @@ def main():
     info0, kt0, lv0 = step(profile=True)
     for _ in range(max(0, args.warmup - 1)):
         step()
-    # The roofline kernel is the CSR SpMV (k_spmv_row on the short-row operators, the tiled k_spmv
-    # on long rows), the dominant kernel family of the step.  In the
+    # The roofline kernel is the CSR SpMV (k_spmv_row on the short-row operators, k_spmv_vec on
+    # longer rows), the dominant kernel family of the step.  In the
     # timed region its top-level-operator launches (the largest instance, 6.29M rows) are timed
     # with CUDA events; timing every small-level launch inside the V-cycle graph would itself slow
     # the solve.  The warm-up step times every class and is reported in config.

@@ -573,8 +573,8 @@ void dev_gather_prolong_f(float* x, int nf, const int* w, cudaStream_t s) {
   if (nf > 0) airg::note_launch(), k_gather_prolong_f<<<grid_for(nf, 256), 256, 0, s>>>(x, nf, w);
 }
 
-// Lanes per row for the tiled SpMV: one thread per row for short rows (the sequential storage-
-// order sum), more lanes as rows grow so that a CTA's 256 / LPR rows hold about one chunk.
+// Lanes per row for the SpMV: one thread per row (k_spmv_row) up to 12 entries per row on average,
+// then LPR lanes per row (k_spmv_vec), about 6 entries per lane.
 int pick_lanes(double L) {
   if (L <= 12.0) return 1;
   if (L <= 24.0) return 2;
