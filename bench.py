@@ -50,6 +50,22 @@ def workload_name(mesh: int) -> str:
             f"block pattern from {{0,1,10}}, theta=0.3, q=1; FP64 AIRG setup + FGMRES(30) solve to rtol 1e-8")
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of a per-rank float over all ranks (x itself without a process group): the
+    job's time is that of its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dofs_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the DOFs every rank solved in `steps` steps, over the slowest rank's time."""
+    return dofs_per_rank * steps * world / seconds
+
+
 def spmv_traffic():
     """DRAM bytes per top-level SpMV launch from the committed ncu summary, or None when the kernel
     source has changed since that capture (the summary records a hash of the kernel's source)."""
@@ -266,12 +282,8 @@ def main():
     torch.cuda.synchronize(dev)
     launches = airg.launch_count() - launches0
     clocks = clk.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = p.n * args.steps * world / (t_ms / 1e3)
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    value = job_value(p.n, args.steps, world, t_ms / 1e3)
 
     # end to end through the public API with host buffers: matrix and rhs copied in from pinned
     # host memory, solution copied back, inside the timed region
@@ -286,12 +298,8 @@ def main():
         H.solve_host(b_h, x_h, rtol=args.rtol, restart=args.restart)
         H.close()
     torch.cuda.synchronize(dev)
-    e_s = time.perf_counter() - e0
-    if dist:
-        tt = torch.tensor([e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
-    e2e = p.n * args.steps * world / e_s
+    e_s = max_over_ranks(time.perf_counter() - e0, dist, dev)
+    e2e = job_value(p.n, args.steps, world, e_s)
 
     peak, peak_kind = peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else None
