@@ -344,13 +344,14 @@ def main():
                        "iters": max(its), "relres": inf["relres"], "dofs_per_s": p.n / (ms / 1e3),
                        "solve_speedup_vs_fp64": round(min(solve_ms) / min(so), 3)}
 
-    # parameter variant the paper sweeps: GMRES-polynomial order 1..6 with first-order fixed sparsity
-    # (the paper's table of orders 1-6), same system, setup and solve to the same rtol
+    # parameter variants the paper sweeps: GMRES-polynomial order 1..6 with first-order fixed
+    # sparsity (the paper's table of orders 1-6) and orders 2, 3, 6 with second-order sparsity; same
+    # system, setup and solve to the same rtol
     poly_sweep = None
     if not args.no_forms:
         poly_sweep = {}
-        for d in range(1, 7):
-            par = airg.Params(poly_order=d)
+        for d, so in [(d, 1) for d in range(1, 7)] + [(2, 2), (3, 2), (6, 2)]:
+            par = airg.Params(poly_order=d, sparsity_order=so)
             Hw = airg.Hierarchy(rp, ci, v, par)
             Hw.solve(b, rtol=args.rtol, restart=args.restart)
             Hw.close()
@@ -362,8 +363,9 @@ def main():
             torch.cuda.synchronize(dev)
             t2 = time.perf_counter()
             Hd.close()
-            poly_sweep[str(d)] = {"setup_ms": round(1e3 * (t1 - t0), 2), "solve_ms": round(1e3 * (t2 - t1), 2),
-                                  "iters": ind["iters"], "status": ind["status"]}
+            poly_sweep[str(d) if so == 1 else f"{d}_second_order_sparsity"] = {
+                "setup_ms": round(1e3 * (t1 - t0), 2), "solve_ms": round(1e3 * (t2 - t1), 2),
+                "iters": ind["iters"], "status": ind["status"]}
 
     # batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle graph,
     # against the same 64 systems solved one after another (same hierarchies)

@@ -89,6 +89,9 @@ typedef struct {
                                stay FP64 in every mode. */
   int keep_setup;           /* 1: keep natural-numbering setup operators for airg_export_level */
   uint64_t seed;            /* seeds PMISR weights and the Box-Muller right-hand sides */
+  int sparsity_order;       /* fixed sparsity of the A_ff polynomials (Section "AIRG"): 1 = pattern of
+                               A_ff (default), 2 = pattern of A_ff^2; the coarsest-level polynomial
+                               always uses first order */
 } airg_params;
 
 typedef struct airg_hierarchy airg_hierarchy; /* opaque, library-owned */

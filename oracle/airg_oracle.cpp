@@ -118,6 +118,7 @@ struct Params {
   int n_smooth_up;
   int one_point_weighted;  // 0: weight 1 (default); reserved
   uint64_t seed;
+  int sparsity_order;      // 1: pattern(A_ff) (default); 2: pattern(A_ff^2)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -453,36 +454,63 @@ Csr with_diag(const Csr& A) {
   return B;
 }
 
-// Steps 7-8 with first-order fixed sparsity, eq. fixed_sparsity.  Reading: the powers are
-// recursive, tilde(A^k) = P_S( tilde(A^{k-1}) A ), with S = pattern(A) plus the diagonal, so row i
-// of each power needs only row i of the previous power and the rows of A in S_i.
-//   tilde(A^k)_ij = sum_{l in S_i, ascending} tilde(A^{k-1})_il a_lj        (fma, a_lj = 0 skipped)
+// Steps 7-8 with fixed sparsity, eq. fixed_sparsity.  Reading: the powers are recursive,
+// tilde(A^k) = P_T( tilde(A^{k-1}) A ), with T = pattern(A) plus the diagonal (first order) or the
+// pattern of that pattern's square (second order, Section "AIRG": "enforcing the sparsity of
+// A_ff^2"), so row i of each power needs only row i of the previous power and the rows of A in T_i.
+//   tilde(A^1) = A on T (zeros where A has no entry)
+//   tilde(A^k)_ij = sum_{l in T_i, ascending} tilde(A^{k-1})_il a_lj     (fma, a_lj absent skipped)
 //   Ainv_ij = alpha_0 delta_ij + alpha_1 tilde(A^1)_ij + ... + alpha_{m-1} tilde(A^{m-1})_ij
 // accumulated left to right with fma.
-Csr fixed_sparsity_inverse(const Csr& A0, const std::vector<double>& alpha) {
-  Csr S = with_diag(A0);
-  int m = (int)alpha.size();
-  Csr Ainv = S;
-  std::vector<double> prev = S.v, cur(S.v.size());
-  for (int i = 0; i < S.nrows; ++i)
+
+// Pattern of S*S (structural; S has its diagonal, so it contains pattern(S)), values: S's entries
+// where S has one, 0 elsewhere.
+Csr square_pattern(const Csr& S) {
+  Csr T;
+  T.nrows = S.nrows;
+  T.ncols = S.ncols;
+  T.rp.assign(1, 0);
+  for (int i = 0; i < S.nrows; ++i) {
+    std::map<int, double> cols;
     for (int k = S.rp[i]; k < S.rp[i + 1]; ++k) {
-      double acc = (S.ci[k] == i && m > 0) ? alpha[0] : 0.0;
+      const int l = S.ci[k];
+      for (int q = S.rp[l]; q < S.rp[l + 1]; ++q) cols.emplace(S.ci[q], 0.0);
+    }
+    for (int k = S.rp[i]; k < S.rp[i + 1]; ++k) cols[S.ci[k]] = S.v[k];
+    for (auto& kv : cols) {
+      T.ci.push_back(kv.first);
+      T.v.push_back(kv.second);
+    }
+    T.rp.push_back((int)T.ci.size());
+  }
+  return T;
+}
+
+Csr fixed_sparsity_inverse(const Csr& A0, const std::vector<double>& alpha, int order) {
+  Csr S = with_diag(A0);
+  Csr T = (order >= 2) ? square_pattern(S) : S;
+  int m = (int)alpha.size();
+  Csr Ainv = T;
+  std::vector<double> prev = T.v, cur(T.v.size());
+  for (int i = 0; i < T.nrows; ++i)
+    for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) {
+      double acc = (T.ci[k] == i && m > 0) ? alpha[0] : 0.0;
       if (m > 1) acc = std::fma(alpha[1], prev[k], acc);
       Ainv.v[k] = acc;
     }
   for (int p = 2; p < m; ++p) {
-    for (int i = 0; i < S.nrows; ++i)
-      for (int k = S.rp[i]; k < S.rp[i + 1]; ++k) {
-        int j = S.ci[k];
+    for (int i = 0; i < T.nrows; ++i)
+      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) {
+        int j = T.ci[k];
         double acc = 0.0;
-        for (int q = S.rp[i]; q < S.rp[i + 1]; ++q) {
-          int l = S.ci[q];
+        for (int q = T.rp[i]; q < T.rp[i + 1]; ++q) {
+          int l = T.ci[q];
           if (has_entry(S, l, j)) acc = std::fma(prev[q], entry(S, l, j), acc);
         }
         cur[k] = acc;
       }
-    for (int i = 0; i < S.nrows; ++i)
-      for (int k = S.rp[i]; k < S.rp[i + 1]; ++k) Ainv.v[k] = std::fma(alpha[p], cur[k], Ainv.v[k]);
+    for (int i = 0; i < T.nrows; ++i)
+      for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) Ainv.v[k] = std::fma(alpha[p], cur[k], Ainv.v[k]);
     std::swap(prev, cur);
   }
   return Ainv;
@@ -656,14 +684,14 @@ void build(Hier& H, const Csr& A0) {
       L.coarsest = true;
       std::vector<double> bt = box_muller(p.seed, l, n);
       L.alpha_fitted = poly_fit(A, mc, bt, L.alpha);
-      L.Ainv = fixed_sparsity_inverse(A, L.alpha);
+      L.Ainv = fixed_sparsity_inverse(A, L.alpha, 1);
       H.lv.push_back(std::move(L));
       return;
     }
     extract(L);
     std::vector<double> bt = box_muller(p.seed, l, (int)L.Fnat.size());
     L.alpha_fitted = poly_fit(L.Aff, m, bt, L.alpha);
-    L.Ainv = fixed_sparsity_inverse(L.Aff, L.alpha);
+    L.Ainv = fixed_sparsity_inverse(L.Aff, L.alpha, p.sparsity_order);
     L.Z = spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false);
     one_point(L, strong);
     Csr Ac = coarse_matrix(L, p.drop_Ac);
@@ -876,6 +904,7 @@ Params to_params(const double* dp, const long long* ip) {
   p.n_smooth_up = (int)ip[6];
   p.one_point_weighted = (int)ip[7];
   p.seed = (uint64_t)ip[8];
+  p.sparsity_order = (int)ip[9];
   return p;
 }
 
@@ -1080,10 +1109,15 @@ int oracle_pattern_nnz(int n, const int* rp, const int* ci) {
   return rp[n] + add;
 }
 int oracle_fixed_sparsity_inverse(int n, const int* rp, const int* ci, const double* v, int m,
-                                  const double* alpha, int* orp, int* oci, double* ov) {
+                                  const double* alpha, int order, int* orp, int* oci, double* ov) {
   Csr A = make_csr(n, n, rp, ci, v);
   std::vector<double> al(alpha, alpha + m);
-  copy_csr(fixed_sparsity_inverse(A, al), orp, oci, ov);
+  Csr R = fixed_sparsity_inverse(A, al, order);
+  if (!oci) {  // sizes only
+    std::copy(R.rp.begin(), R.rp.end(), orp);
+    return 0;
+  }
+  copy_csr(R, orp, oci, ov);
   return 0;
 }
 

@@ -66,12 +66,13 @@ class Params:
     n_smooth_up: int = 2
     one_point_weighted: int = 0
     seed: int = 240808262
+    sparsity_order: int = 1
 
     def arrays(self):
         dp = np.array([self.strong_threshold, self.ddc_fraction, self.drop_R, self.drop_Ac], dtype=np.float64)
         ip = np.array([self.pmisr_max_loops, self.poly_order, self.coarse_poly_order, self.coarse_iters,
                        self.coarse_size, self.max_levels, self.n_smooth_up, self.one_point_weighted,
-                       self.seed & 0x7FFFFFFFFFFFFFFF], dtype=np.int64)
+                       self.seed & 0x7FFFFFFFFFFFFFFF, self.sparsity_order], dtype=np.int64)
         return dp, ip
 
 
@@ -253,17 +254,18 @@ def unif01(seed: int, level: int, stream: int, n: int):
     return r
 
 
-def fixed_sparsity_inverse(rowptr, col, val, alpha):
+def fixed_sparsity_inverse(rowptr, col, val, alpha, order: int = 1):
     rp, ci, v = _csr(rowptr, col, val)
     n = len(rp) - 1
     al = np.ascontiguousarray(alpha, dtype=np.float64)
-    nz = lib().oracle_pattern_nnz(C.c_int(n), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p))
     orp = np.zeros(n + 1, dtype=np.int32)
+    args = (C.c_int(n), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+            C.c_int(len(al)), al.ctypes.data_as(C.c_void_p), C.c_int(order))
+    lib().oracle_fixed_sparsity_inverse(*args, orp.ctypes.data_as(C.c_void_p), None, None)
+    nz = int(orp[-1])
     oci = np.zeros(nz, dtype=np.int32)
     ov = np.zeros(nz)
-    lib().oracle_fixed_sparsity_inverse(C.c_int(n), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
-                                        v.ctypes.data_as(C.c_void_p), C.c_int(len(al)), al.ctypes.data_as(C.c_void_p),
-                                        orp.ctypes.data_as(C.c_void_p), oci.ctypes.data_as(C.c_void_p),
+    lib().oracle_fixed_sparsity_inverse(*args, orp.ctypes.data_as(C.c_void_p), oci.ctypes.data_as(C.c_void_p),
                                         ov.ctypes.data_as(C.c_void_p))
     return orp, oci, ov
 

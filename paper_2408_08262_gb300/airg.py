@@ -38,7 +38,8 @@ class _Params(C.Structure):
     _fields_ = [("strong_threshold", C.c_double), ("ddc_fraction", C.c_double), ("pmisr_max_loops", C.c_int),
                 ("poly_order", C.c_int), ("coarse_poly_order", C.c_int), ("coarse_iters", C.c_int),
                 ("coarse_size", C.c_int), ("max_levels", C.c_int), ("drop_R", C.c_double), ("drop_Ac", C.c_double),
-                ("n_smooth_up", C.c_int), ("precision", C.c_int), ("keep_setup", C.c_int), ("seed", C.c_uint64)]
+                ("n_smooth_up", C.c_int), ("precision", C.c_int), ("keep_setup", C.c_int), ("seed", C.c_uint64),
+                ("sparsity_order", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -118,6 +119,7 @@ class Params:
     precision: int = 0
     keep_setup: int = 0
     seed: int = 240808262
+    sparsity_order: int = 1
 
     def c(self) -> _Params:
         return _Params(**{k: getattr(self, k) for k, _ in _Params._fields_})

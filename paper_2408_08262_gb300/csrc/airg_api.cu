@@ -32,6 +32,7 @@ SetupParams to_setup(const airg_params& p) {
   q.max_levels = p.max_levels;
   q.n_smooth_up = p.n_smooth_up;
   q.seed = p.seed;
+  q.sparsity_order = p.sparsity_order;
   return q;
 }
 
@@ -43,6 +44,7 @@ int check_params(const airg_params* p) {
   if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0) return AIRG_ERR_ARG;
   if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
   if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
+  if (p->sparsity_order != 1 && p->sparsity_order != 2) return AIRG_ERR_ARG;
   return AIRG_OK;
 }
 
@@ -306,6 +308,7 @@ void airg_params_default(airg_params* p) {
   p->precision = AIRG_FP64;
   p->keep_setup = 0;
   p->seed = 240808262ULL;
+  p->sparsity_order = 1;
 }
 
 int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {

@@ -170,6 +170,7 @@ struct SetupParams {
   double strong_threshold, ddc_fraction, drop_R, drop_Ac;
   int pmisr_max_loops, poly_order, coarse_poly_order, coarse_iters, coarse_size, max_levels, n_smooth_up;
   uint64_t seed;
+  int sparsity_order = 1;  // fixed sparsity of the A_ff polynomials: 1 pattern(A_ff), 2 pattern(A_ff^2)
 };
 
 // CF splitting of A (natural numbering); cf: device int8 n (1 F, 2 C).  strong (device uint8 nnz)
@@ -182,9 +183,10 @@ int cf_split(const DCsr& A, const SetupParams& p, int level, int8_t* cf, uint8_t
 int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int* fitted, Arena& tmp,
              cudaStream_t s);
 
-// First-order fixed-sparsity approximate inverse on the pattern of A (diagonal required).
+// Fixed-sparsity approximate inverse on the pattern of A (order 1) or of A^2 (order 2); A must store
+// its diagonal.
 int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out, Arena& own, Arena& tmp,
-                           cudaStream_t s);
+                           cudaStream_t s, int order);
 
 // C = scale * (A B) with the relative row-wise inf-norm drop (|c| < tol max|c_i.| dropped; the
 // diagonal kept when keep_diag).

@@ -907,43 +907,54 @@ __global__ void k_fs_rowsq(int n, const int* __restrict__ rp, long long* __restr
     sq[i] = r * r;
   }
 }
-__global__ void k_fs_gather(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
-                            const int* __restrict__ ci, const long long* __restrict__ ntot, long long cap,
-                            const long long* __restrict__ base, int* __restrict__ idx) {
+__global__ void k_fs_gather(int nnz, const int* __restrict__ rowidx, const int* __restrict__ prp,
+                            const int* __restrict__ pci, const int* __restrict__ arp, const int* __restrict__ aci,
+                            const long long* __restrict__ ntot, long long cap, const long long* __restrict__ base,
+                            int* __restrict__ idx) {
   if (*ntot > cap) return;  // too large: the powers search instead
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
-    const int i = rowidx[k], j = ci[k];
-    const int b = rp[i], r = rp[i + 1] - b;
+    const int i = rowidx[k], j = pci[k];
+    const int b = prp[i], r = prp[i + 1] - b;
     int* o = idx + base[i] + (long long)(k - b) * r;
     for (int q = 0; q < r; ++q) {
-      const int l = ci[b + q];
-      o[q] = find_col(ci, rp[l], rp[l + 1], j);
+      const int l = pci[b + q];
+      o[q] = find_col(aci, arp[l], arp[l + 1], j);
     }
   }
 }
-__global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* __restrict__ rp,
-                           const int* __restrict__ ci, const long long* __restrict__ ntot, long long cap,
-                           const long long* __restrict__ base, const int* __restrict__ idx,
-                           const double* __restrict__ v, const double* __restrict__ prev, double* __restrict__ cur,
-                           double* __restrict__ ainv, const double* __restrict__ alpha_p) {
+// Values of A on a larger pattern P (second-order sparsity): a_ij where A has the entry, else 0.
+__global__ void k_fs_scatter(int nnz, const int* __restrict__ rowidx, const int* __restrict__ pci,
+                             const int* __restrict__ arp, const int* __restrict__ aci, const double* __restrict__ av,
+                             double* __restrict__ p1) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int i = rowidx[k];
+    const int t = find_col(aci, arp[i], arp[i + 1], pci[k]);
+    p1[k] = t >= 0 ? av[t] : 0.0;
+  }
+}
+__global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* __restrict__ prp,
+                           const int* __restrict__ pci, const int* __restrict__ arp, const int* __restrict__ aci,
+                           const long long* __restrict__ ntot, long long cap, const long long* __restrict__ base,
+                           const int* __restrict__ idx, const double* __restrict__ av, const double* __restrict__ prev,
+                           double* __restrict__ cur, double* __restrict__ ainv, const double* __restrict__ alpha_p) {
   const double ap = *alpha_p;
   const bool gathered = *ntot <= cap;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
     const int i = rowidx[k];
-    const int b = rp[i], r = rp[i + 1] - b;
+    const int b = prp[i], r = prp[i + 1] - b;
     double acc = 0.0;
     if (gathered) {
       const int* g = idx + base[i] + (long long)(k - b) * r;
       for (int q = 0; q < r; ++q) {
         const int t = g[q];
-        if (t >= 0) acc = fma(prev[b + q], v[t], acc);
+        if (t >= 0) acc = fma(prev[b + q], av[t], acc);
       }
     } else {  // rows of hundreds of entries (dense coarse levels): search every position
-      const int j = ci[k];
+      const int j = pci[k];
       for (int q = b; q < b + r; ++q) {
-        const int l = ci[q];
-        const int t = find_col(ci, rp[l], rp[l + 1], j);
-        if (t >= 0) acc = fma(prev[q], v[t], acc);
+        const int l = pci[q];
+        const int t = find_col(aci, arp[l], arp[l + 1], j);
+        if (t >= 0) acc = fma(prev[q], av[t], acc);
       }
     }
     cur[k] = acc;
@@ -952,16 +963,28 @@ __global__ void k_fs_power(int nnz, const int* __restrict__ rowidx, const int* _
 }
 
 int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out, Arena& own, Arena& tmp,
-                           cudaStream_t s) {
-  const int n = A.nrows, nnz = A.nnz;
+                           cudaStream_t s, int order) {
+  const int n = A.nrows;
+  // the pattern P of the powers: A's own (first order) or that of A^2 (second order); A has its
+  // diagonal, so pattern(A^2) contains pattern(A)
+  DCsr Pt = A;
+  if (order >= 2 && A.nnz > 0) AIRG_TRY(spgemm(A, A, 1.0, 0.0, false, Pt, tmp, tmp, s));
+  const int nnz = Pt.nnz;
   AIRG_TRY(own.csr(out, n, n, nnz));
-  CU_TRY(cudaMemcpyAsync(out.rp, A.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
-  CU_TRY(cudaMemcpyAsync(out.ci, A.ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(out.rp, Pt.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+  CU_TRY(cudaMemcpyAsync(out.ci, Pt.ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice, s));
   if (nnz == 0) return AIRG_OK;
   int* rowidx;
   AIRG_TRY(tmp.alloc(&rowidx, nnz));
-  airg::note_launch(), k_row_index<<<GRID(n)>>>(n, A.rp, rowidx);
-  airg::note_launch(), k_fs_init<<<GRID(nnz)>>>(nnz, rowidx, A.ci, A.v, alpha, m, out.v);
+  airg::note_launch(), k_row_index<<<GRID(n)>>>(n, Pt.rp, rowidx);
+  const double* p1 = A.v;  // tilde(A^1): A on the pattern
+  if (Pt.rp != A.rp) {
+    double* sc;
+    AIRG_TRY(tmp.alloc(&sc, nnz));
+    airg::note_launch(), k_fs_scatter<<<GRID(nnz)>>>(nnz, rowidx, Pt.ci, A.rp, A.ci, A.v, sc);
+    p1 = sc;
+  }
+  airg::note_launch(), k_fs_init<<<GRID(nnz)>>>(nnz, rowidx, Pt.ci, p1, alpha, m, out.v);
   KERNEL_CHECK();
   if (m > 2) {
     double *pa, *pb;
@@ -971,19 +994,19 @@ int fixed_sparsity_inverse(const DCsr& A, const double* alpha, int m, DCsr& out,
     AIRG_TRY(tmp.alloc(&pb, nnz));
     AIRG_TRY(tmp.alloc(&sq, n));
     AIRG_TRY(tmp.alloc(&base, (size_t)n + 1));
-    airg::note_launch(), k_fs_rowsq<<<GRID(n)>>>(n, A.rp, sq);
+    airg::note_launch(), k_fs_rowsq<<<GRID(n)>>>(n, Pt.rp, sq);
     // the gathered index costs sum_i r_i^2 ints: it is used when that is at most 128 per nonzero
     // (and 2 GiB), decided on the device from base[n]; otherwise every power searches
     AIRG_TRY(scan_i64(sq, base, n, tmp, s, nullptr));
     const long long cap = std::min(128LL * nnz, 1LL << 29);
     AIRG_TRY(tmp.alloc(&idx, (size_t)cap));
-    airg::note_launch(), k_fs_gather<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, base + n, cap, base, idx);
+    airg::note_launch(), k_fs_gather<<<GRID(nnz)>>>(nnz, rowidx, Pt.rp, Pt.ci, A.rp, A.ci, base + n, cap, base, idx);
     KERNEL_CHECK();
-    const double* prev = A.v;
+    const double* prev = p1;
     double* cur = pa;
     for (int p = 2; p < m; ++p) {
-      airg::note_launch(), k_fs_power<<<GRID(nnz)>>>(nnz, rowidx, A.rp, A.ci, base + n, cap, base, idx, A.v, prev, cur,
-                                                     out.v, alpha + p);
+      airg::note_launch(), k_fs_power<<<GRID(nnz)>>>(nnz, rowidx, Pt.rp, Pt.ci, A.rp, A.ci, base + n, cap, base, idx,
+                                                     A.v, prev, cur, out.v, alpha + p);
       KERNEL_CHECK();
       prev = cur;
       cur = (cur == pa) ? pb : pa;
@@ -1804,7 +1827,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
     AIRG_TRY(own.alloc(&L.alpha, mc));
     AIRG_TRY(own.alloc(&L.fitted_dev, 1));
     AIRG_TRY(poly_fit(A, mc, p.seed, level, L.alpha, L.fitted_dev, tmp, s));
-    AIRG_TRY(fixed_sparsity_inverse(A, L.alpha, mc, L.Ainv, own, tmp, s));
+    AIRG_TRY(fixed_sparsity_inverse(A, L.alpha, mc, L.Ainv, own, tmp, s, 1));
     mark(2);
     mark(3);
     mark(4);
@@ -1855,7 +1878,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   AIRG_TRY(own.alloc(&L.alpha, m));
   AIRG_TRY(own.alloc(&L.fitted_dev, 1));
   AIRG_TRY(poly_fit(L.Aff, m, p.seed, level, L.alpha, L.fitted_dev, tmp, s));
-  AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s));
+  AIRG_TRY(fixed_sparsity_inverse(L.Aff, L.alpha, m, L.Ainv, own, tmp, s, p.sparsity_order));
   // steps 10-11a (one-point P and A P) need only the splitting: on the side stream, they overlap
   // the polynomial fit
   AIRG_TRY(own.alloc(&L.w, nf));

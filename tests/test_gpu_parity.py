@@ -38,7 +38,7 @@ def gpu_params(op: O.Params, keep=1) -> airg.Params:
                        pmisr_max_loops=op.pmisr_max_loops, poly_order=op.poly_order,
                        coarse_poly_order=op.coarse_poly_order, coarse_iters=op.coarse_iters,
                        coarse_size=op.coarse_size, max_levels=op.max_levels, drop_R=op.drop_R, drop_Ac=op.drop_Ac,
-                       n_smooth_up=op.n_smooth_up, keep_setup=keep, seed=op.seed)
+                       n_smooth_up=op.n_smooth_up, keep_setup=keep, seed=op.seed, sparsity_order=op.sparsity_order)
 
 
 def assert_csr_close(a, b, rtol=1e-10, what=""):
@@ -97,10 +97,10 @@ def test_cf_split_bitexact_on_oracle_coarse_levels():
 # One level of setup on identical input
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mesh,order", [(64, 2), (48, 6), (20, 3)])
-def test_level_operators_match_oracle(mesh, order):
+@pytest.mark.parametrize("mesh,order,sparsity", [(64, 2, 1), (48, 6, 1), (20, 3, 1), (48, 6, 2), (40, 3, 2)])
+def test_level_operators_match_oracle(mesh, order, sparsity):
     p = P.p1_dg_2d(mesh, 0.3, seed=3 + mesh, sigma_uniform=(0.0, 2.0))
-    op = O.Params(poly_order=order, max_levels=2, coarse_size=0)
+    op = O.Params(poly_order=order, max_levels=2, coarse_size=0, sparsity_order=sparsity)
     Ho = O.Hierarchy(p.rowptr, p.col, p.val, op)
     Hg = airg.Hierarchy(*dev(p), gpu_params(op))
     assert Hg.num_levels == Ho.num_levels == 2
@@ -245,6 +245,15 @@ def test_solution_matches_oracle(mesh, degree):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
     assert abs(ig["iters"] - io["iters"]) <= 1
     assert ig["relres"] <= 1e-12
+
+
+@pytest.mark.parametrize("mesh,degree", [(48, 2), (48, 6)])
+def test_second_order_sparsity_solution_matches_oracle(mesh, degree):
+    p = P.streaming_2d(mesh)
+    xo, io, xg, ig, _ = solve_both(p, O.Params(poly_order=degree, sparsity_order=2))
+    assert ig["status"] == 0 and io["status"] == 0
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    assert abs(ig["iters"] - io["iters"]) <= 1
 
 
 def test_polynomial_order_trend():

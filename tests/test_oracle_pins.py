@@ -327,6 +327,41 @@ def test_fixed_sparsity_closed_pattern_equals_true_powers():
     np.testing.assert_allclose(dense(r, c, v), ref, rtol=1e-12, atol=1e-12)
 
 
+def test_second_order_sparsity_is_exact_for_degree_two_on_a_tridiagonal_matrix():
+    # Section "AIRG": second-order fixed sparsity enforces the pattern of A_ff^2.  For a tridiagonal
+    # A that pattern is pentadiagonal and holds A^2 exactly, so the degree-2 polynomial is exact,
+    # while first order (tridiagonal) truncates A^2.
+    n = 14
+    rng = np.random.default_rng(12)
+    M = np.diag(4 + rng.random(n)) + np.diag(rng.standard_normal(n - 1), -1) + np.diag(rng.standard_normal(n - 1), 1)
+    alpha = np.array([0.7, -0.2, 0.05])
+    ref = alpha[0] * np.eye(n) + alpha[1] * M + alpha[2] * M @ M
+    r, c, v = O.fixed_sparsity_inverse(*to_csr(M), alpha, order=2)
+    assert np.diff(r).max() == 5  # pentadiagonal
+    np.testing.assert_allclose(dense(r, c, v), ref, rtol=1e-14, atol=1e-14)
+    r1, c1, v1 = O.fixed_sparsity_inverse(*to_csr(M), alpha, order=1)
+    assert np.abs(dense(r1, c1, v1) - ref).max() > 1e-3
+
+
+def test_second_order_sparsity_matches_a_dense_masked_recursion():
+    # tilde(A^k) = mask(tilde(A^{k-1}) A) with mask = pattern(A^2), computed densely
+    A = sp.random(30, 30, density=0.08, random_state=21, format="csr") + 3 * sp.eye(30)
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    D = A.toarray()
+    mask = (np.abs((A != 0).astype(float) @ (A != 0).astype(float)).toarray() > 0)
+    alpha = np.array([0.5, -0.3, 0.2, -0.1, 0.05])
+    P = D * mask
+    ref = alpha[0] * np.eye(30) + alpha[1] * P
+    for k in range(2, len(alpha)):
+        P = (P @ D) * mask
+        ref = ref + alpha[k] * P
+    r, c, v = O.fixed_sparsity_inverse(A.indptr, A.indices, A.data, alpha, order=2)
+    got = dense(r, c, v)
+    assert np.array_equal(got != 0, (ref != 0) | (got != 0))  # pattern contains every nonzero
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13)
+
+
 # ---------------------------------------------------------------------------------------------
 # Products, coarse matrix, operators
 # ---------------------------------------------------------------------------------------------
