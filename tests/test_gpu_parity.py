@@ -257,7 +257,7 @@ def test_second_order_sparsity_solution_matches_oracle(mesh, degree):
 
 
 def test_polynomial_order_trend():
-    """Section "Parallel results" (GMRES-polynomial table): with first-order fixed sparsity the
+    """Section "GMRES polynomial order" (table of orders 1-6): with first-order fixed sparsity the
     iteration count falls steeply from order 1 and flattens by order 4-6."""
     p = P.blocked_sigma_2d(256)
     b = torch.from_numpy(p.b).cuda()
