@@ -345,13 +345,16 @@ def main():
                        "solve_speedup_vs_fp64": round(min(solve_ms) / min(so), 3)}
 
     # parameter variants the paper sweeps: GMRES-polynomial order 1..6 with first-order fixed
-    # sparsity (the paper's table of orders 1-6) and orders 2, 3, 6 with second-order sparsity; same
-    # system, setup and solve to the same rtol
+    # sparsity (the paper's table of orders 1-6), orders 2, 3, 6 with second-order sparsity, orders 3
+    # and 6 with every polynomial applied matrix-free, and order 6 with the approximate ideal
+    # prolongator; same system, setup and solve to the same rtol
     poly_sweep = None
     if not args.no_forms:
         poly_sweep = {}
-        for d, so in [(d, 1) for d in range(1, 7)] + [(2, 2), (3, 2), (6, 2)]:
-            par = airg.Params(poly_order=d, sparsity_order=so)
+        variants = ([(d, 1, 0, 0) for d in range(1, 7)] + [(2, 2, 0, 0), (3, 2, 0, 0), (6, 2, 0, 0)] +
+                    [(3, 1, 1, 0), (6, 1, 1, 0), (6, 1, 0, 1)])
+        for d, so, mf, ip in variants:
+            par = airg.Params(poly_order=d, sparsity_order=so, matrix_free=mf, ideal_prolong=ip)
             Hw = airg.Hierarchy(rp, ci, v, par)
             Hw.solve(b, rtol=args.rtol, restart=args.restart)
             Hw.close()
@@ -363,7 +366,9 @@ def main():
             torch.cuda.synchronize(dev)
             t2 = time.perf_counter()
             Hd.close()
-            poly_sweep[str(d) if so == 1 else f"{d}_second_order_sparsity"] = {
+            key = (f"{d}_matrix_free" if mf else f"{d}_ideal_prolong" if ip else
+                   str(d) if so == 1 else f"{d}_second_order_sparsity")
+            poly_sweep[key] = {
                 "setup_ms": round(1e3 * (t1 - t0), 2), "solve_ms": round(1e3 * (t2 - t1), 2),
                 "iters": ind["iters"], "status": ind["status"]}
 

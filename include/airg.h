@@ -92,6 +92,14 @@ typedef struct {
   int sparsity_order;       /* fixed sparsity of the A_ff polynomials (Section "AIRG"): 1 = pattern of
                                A_ff (default), 2 = pattern of A_ff^2; the coarsest-level polynomial
                                always uses first order */
+  int matrix_free;          /* 1: the solve applies every polynomial matrix-free, q(A_ff) r by Horner's
+                               rule with m - 1 products by A_ff (q(A) r with the coarsest matrix), in
+                               place of the assembled fixed-sparsity inverse (Section "AIRG" names this
+                               alternative); setup still assembles Ainv for Z.  FP64 only; 0 (default):
+                               assembled */
+  int ideal_prolong;        /* 1: approximate ideal prolongator P = [W; I], W = -Ainv A_fc (eq. prolong)
+                               with drop_R's relative drop, in place of the one-point operator (setup
+                               step 10's alternative); FP64 only; 0 (default): one-point */
 } airg_params;
 
 typedef struct airg_hierarchy airg_hierarchy; /* opaque, library-owned */
@@ -153,7 +161,9 @@ int airg_sddmm(const airg_csr* pattern, const double* lam, const double* x, doub
  * into grouped CSR matrices (columns relabelled to positions in one concatenated vector, rows
  * mapped to their positions), so every V-cycle step is one launch over all systems; the batched
  * V-cycle is captured once as a CUDA graph.  The hierarchies must outlive the batch and share
- * coarse_iters and n_smooth_up.  airg_solve_batched runs right-preconditioned FGMRES on every system
+ * coarse_iters and n_smooth_up, and use assembled polynomials and one-point prolongators
+ * (matrix_free = ideal_prolong = 0; else AIRG_ERR_ARG).
+ * airg_solve_batched runs right-preconditioned FGMRES on every system
  * in lockstep, with per-system (segmented) reductions and per-system convergence: b[q], x[q] are
  * device pointers of system q's size (x holds the initial guess unless opts->x0_zero), infos has
  * nsys entries.  Returns the worst status (a negative error if any system failed). */
@@ -196,11 +206,11 @@ void airg_free(airg_hierarchy* H);
 /* Number of levels (>= 1), or a negative error. */
 int airg_num_levels(const airg_hierarchy* H);
 
-/* Per-level sizes into info[0..15] (host): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
+/* Per-level sizes into info[0..16] (host, 17 entries): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
  * nnz(Z), coarsest flag, nnz(A_cf), fitted polynomial coefficients, nnz(AF solve operator), and the
  * level's setup time in microseconds split as in the paper's per-component setup figure:
  * [12] CF splitting + extraction, [13] GMRES polynomial (steps 3-8), [14] restrictor product,
- * [15] prolongator + coarse matrix.
+ * [15] prolongator + coarse matrix; [16] nnz(W) of the approximate ideal prolongator (0 for one-point).
  * Level -1 gives totals: [0] levels, [1] grid complexity x1e6, [2] operator complexity x1e6,
  * [3] storage complexity x1e6 (eq. mat_store), [4] setup wall ms x1e3, [5..9] summed microseconds of
  * the five phases (CF splitting, extraction, polynomial, restrictor, prolongator + coarse matrix),
@@ -214,7 +224,10 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info);
  * Solve-phase layout (always available): 7 [A_ff A_fc] rows of the F-points with columns in the
  *   level's F-then-C numbering (nnz = info[11]), 8 Z with rows in the next level's F-then-C
  *   numbering, 9 the top-level matrix permuted to level 0's F-then-C numbering (n0 x n0, nnz of
- *   the input), 10 Ainv as used by the solve, 11 coarsest-level matrix.
+ *   the input), 10 Ainv as used by the solve, 11 coarsest-level matrix, 13 W with columns in the
+ *   next level's F-then-C numbering (ideal_prolong only).
+ * 12: W in natural numbering (rows F-points, columns C-points, ascending; needs keep_setup and
+ *   ideal_prolong).
  * Any of rowptr/col/val may be NULL. */
 int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowptr, int32_t* col, double* val);
 

@@ -119,6 +119,8 @@ struct Params {
   int one_point_weighted;  // 0: weight 1 (default); reserved
   uint64_t seed;
   int sparsity_order;      // 1: pattern(A_ff) (default); 2: pattern(A_ff^2)
+  int matrix_free;         // 1: the V-cycle applies q(A_ff) (q(A) on the coarsest) from its definition
+  int ideal_prolong;       // 1: approximate ideal prolongator W = -Ainv A_fc (eq. prolong) for P
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -560,6 +562,7 @@ struct Level {
   std::vector<int> fidx, cidx, Fnat, Cnat;
   Csr Aff, Afc, Acf, Acc, Ainv, Z;
   std::vector<int> w;        // one-point prolongation: F index -> C index (-1: none)
+  Csr W;                     // approximate ideal prolongator (n_f x n_c); empty for one-point P
   std::vector<double> alpha;
   int alpha_fitted = 0;
   int rounds = 0;
@@ -630,7 +633,8 @@ void one_point(Level& L, const std::vector<int8_t>& strong) {
   }
 }
 
-// Coarse matrix (setup step 11): A_c = R (A P), P = [W; I], R = [Z I] in natural numbering.
+// Coarse matrix (setup step 11): A_c = R (A P), P = [W; I], R = [Z I] in natural numbering.  W is
+// the approximate ideal prolongator when the level has one, else the one-point operator.
 Csr coarse_matrix(const Level& L, double drop) {
   const Csr& A = L.A;
   int n = A.nrows, nc = (int)L.Cnat.size();
@@ -638,9 +642,15 @@ Csr coarse_matrix(const Level& L, double drop) {
   P.nrows = n;
   P.ncols = nc;
   P.rp.assign(1, 0);
+  const bool ideal = L.W.nrows > 0;
   for (int i = 0; i < n; ++i) {
-    int c = (L.cf[i] == C) ? L.cidx[i] : L.w[L.fidx[i]];
-    if (c >= 0) { P.ci.push_back(c); P.v.push_back(1.0); }
+    if (ideal && L.cf[i] == F) {
+      int f = L.fidx[i];
+      for (int k = L.W.rp[f]; k < L.W.rp[f + 1]; ++k) { P.ci.push_back(L.W.ci[k]); P.v.push_back(L.W.v[k]); }
+    } else {
+      int c = (L.cf[i] == C) ? L.cidx[i] : L.w[L.fidx[i]];
+      if (c >= 0) { P.ci.push_back(c); P.v.push_back(1.0); }
+    }
     P.rp.push_back((int)P.ci.size());
   }
   Csr AP = spgemm(A, P, 1.0, 0.0, false);
@@ -694,6 +704,9 @@ void build(Hier& H, const Csr& A0) {
     L.Ainv = fixed_sparsity_inverse(L.Aff, L.alpha, p.sparsity_order);
     L.Z = spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false);
     one_point(L, strong);
+    // setup step 10's alternative: the prolongator's counterpart of Z (eq. prolong),
+    // W = -Ainv A_fc, with Z's relative drop tolerance
+    if (p.ideal_prolong) L.W = spgemm(L.Ainv, L.Afc, -1.0, p.drop_R, false);
     Csr Ac = coarse_matrix(L, p.drop_Ac);
     H.lv.push_back(std::move(L));
     A = std::move(Ac);
@@ -706,8 +719,25 @@ void build(Hier& H, const Csr& A0) {
 // V-cycle (Section "Results"): zero initial guess, restriction with R = [Z I], recursion,
 // one-point prolongation, then n_smooth_up F-point smooths x_F += Ainv (b_F - A_ff x_F - A_fc x_C);
 // no down-smoothing.  Coarsest level: coarse_iters iterations of x += Ainv_L (b - A_L x).
+// The stationary polynomial applied without assembling it (Section "AIRG" names this alternative
+// to the fixed-sparsity matrix): t = q(A) r = sum_{k<m} alpha_k A^k r, from the power basis
+// v_0 = r, v_k = A v_{k-1}.
+void poly_apply(const Csr& A, const std::vector<double>& alpha, const std::vector<double>& r, std::vector<double>& t) {
+  int n = A.nrows;
+  t.assign(n, 0.0);
+  std::vector<double> v = r, Av;
+  for (size_t k = 0; k < alpha.size(); ++k) {
+    if (k > 0) {
+      spmv(A, v, Av);
+      v.swap(Av);
+    }
+    for (int i = 0; i < n; ++i) t[i] += alpha[k] * v[i];
+  }
+}
+
 void vcycle(const Hier& H, int l, const std::vector<double>& b, std::vector<double>& x) {
   const Level& L = H.lv[l];
+  const bool mf = H.p.matrix_free != 0;
   int n = L.A.nrows;
   x.assign(n, 0.0);
   if (L.coarsest) {
@@ -715,7 +745,8 @@ void vcycle(const Hier& H, int l, const std::vector<double>& b, std::vector<doub
     for (int it = 0; it < H.p.coarse_iters; ++it) {
       spmv(L.A, x, t);
       for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
-      spmv(L.Ainv, r, t);
+      if (mf) poly_apply(L.A, L.alpha, r, t);
+      else spmv(L.Ainv, r, t);
       for (int i = 0; i < n; ++i) x[i] += t[i];
     }
     return;
@@ -727,13 +758,16 @@ void vcycle(const Hier& H, int l, const std::vector<double>& b, std::vector<doub
   spmv(L.Z, bF, t);
   for (int c = 0; c < nc; ++c) bC[c] += t[c];
   vcycle(H, l + 1, bC, xC);
-  for (int f = 0; f < nf; ++f) xF[f] = (L.w[f] >= 0) ? xC[L.w[f]] : 0.0;
+  if (L.W.nrows > 0) spmv(L.W, xC, xF);  // x_F = W x_C
+  else
+    for (int f = 0; f < nf; ++f) xF[f] = (L.w[f] >= 0) ? xC[L.w[f]] : 0.0;
   std::vector<double> r(nf), t2;
   for (int s = 0; s < H.p.n_smooth_up; ++s) {
     spmv(L.Aff, xF, t);
     spmv(L.Afc, xC, t2);
     for (int f = 0; f < nf; ++f) r[f] = bF[f] - t[f] - t2[f];
-    spmv(L.Ainv, r, t);
+    if (mf) poly_apply(L.Aff, L.alpha, r, t);
+    else spmv(L.Ainv, r, t);
     for (int f = 0; f < nf; ++f) xF[f] += t[f];
   }
   for (int f = 0; f < nf; ++f) x[L.Fnat[f]] = xF[f];
@@ -905,6 +939,8 @@ Params to_params(const double* dp, const long long* ip) {
   p.one_point_weighted = (int)ip[7];
   p.seed = (uint64_t)ip[8];
   p.sparsity_order = (int)ip[9];
+  p.matrix_free = (int)ip[10];
+  p.ideal_prolong = (int)ip[11];
   return p;
 }
 
@@ -958,11 +994,12 @@ int oracle_level_info(void* h, int l, long long* info, double* tau) {
   info[9] = L.rounds;
   info[10] = L.alpha_fitted;
   info[11] = L.Acf.nnz();
+  info[12] = L.W.nnz();
   if (tau) *tau = L.tau;
   return 0;
 }
 
-// which: 0 A, 1 Aff, 2 Afc, 3 Acf, 4 Acc, 5 Ainv, 6 Z  (CSR export; call with the sizes from
+// which: 0 A, 1 Aff, 2 Afc, 3 Acf, 4 Acc, 5 Ainv, 6 Z, 7 W  (CSR export; call with the sizes from
 // oracle_level_info).
 int oracle_export_csr(void* h, int l, int which, int* rp, int* ci, double* v) {
   Hier* H = (Hier*)h;
@@ -977,6 +1014,7 @@ int oracle_export_csr(void* h, int l, int which, int* rp, int* ci, double* v) {
     case 4: M = &L.Acc; break;
     case 5: M = &L.Ainv; break;
     case 6: M = &L.Z; break;
+    case 7: M = &L.W; break;
     default: return -1;
   }
   copy_csr(*M, rp, ci, v);

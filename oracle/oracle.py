@@ -67,12 +67,14 @@ class Params:
     one_point_weighted: int = 0
     seed: int = 240808262
     sparsity_order: int = 1
+    matrix_free: int = 0
+    ideal_prolong: int = 0
 
     def arrays(self):
         dp = np.array([self.strong_threshold, self.ddc_fraction, self.drop_R, self.drop_Ac], dtype=np.float64)
         ip = np.array([self.pmisr_max_loops, self.poly_order, self.coarse_poly_order, self.coarse_iters,
                        self.coarse_size, self.max_levels, self.n_smooth_up, self.one_point_weighted,
-                       self.seed & 0x7FFFFFFFFFFFFFFF, self.sparsity_order], dtype=np.int64)
+                       self.seed & 0x7FFFFFFFFFFFFFFF, self.sparsity_order, self.matrix_free, self.ideal_prolong], dtype=np.int64)
         return dp, ip
 
 
@@ -105,25 +107,26 @@ class Hierarchy:
         return lib().oracle_num_levels(self._h)
 
     def level_info(self, l: int) -> dict:
-        info = np.zeros(12, dtype=np.int64)
+        info = np.zeros(13, dtype=np.int64)
         tau = C.c_double()
         rc = lib().oracle_level_info(self._h, C.c_int(l), info.ctypes.data_as(C.c_void_p), C.byref(tau))
         if rc:
             raise IndexError(l)
         keys = ["n", "nnz", "nf", "nc", "nnz_aff", "nnz_afc", "nnz_ainv", "nnz_z", "coarsest", "rounds",
-                "alpha_fitted", "nnz_acf"]
+                "alpha_fitted", "nnz_acf", "nnz_w"]
         d = {k: int(x) for k, x in zip(keys, info)}
         d["tau"] = tau.value
         return d
 
     def export(self, l: int, which: str):
-        """CSR export of a level operator: A, Aff, Afc, Acf, Acc, Ainv, Z."""
-        code = {"A": 0, "Aff": 1, "Afc": 2, "Acf": 3, "Acc": 4, "Ainv": 5, "Z": 6}[which]
+        """CSR export of a level operator: A, Aff, Afc, Acf, Acc, Ainv, Z, W (ideal prolongator)."""
+        code = {"A": 0, "Aff": 1, "Afc": 2, "Acf": 3, "Acc": 4, "Ainv": 5, "Z": 6, "W": 7}[which]
         info = self.level_info(l)
         rows = {"A": info["n"], "Aff": info["nf"], "Afc": info["nf"], "Acf": info["nc"], "Acc": info["nc"],
-                "Ainv": info["nf"] if not info["coarsest"] else info["n"], "Z": info["nc"]}[which]
+                "Ainv": info["nf"] if not info["coarsest"] else info["n"], "Z": info["nc"],
+                "W": info["nf"] if info["nnz_w"] or self.params.ideal_prolong else 0}[which]
         nnz = {"A": info["nnz"], "Aff": info["nnz_aff"], "Afc": info["nnz_afc"], "Acf": info["nnz_acf"],
-               "Ainv": info["nnz_ainv"], "Z": info["nnz_z"], "Acc": None}[which]
+               "Ainv": info["nnz_ainv"], "Z": info["nnz_z"], "W": info["nnz_w"], "Acc": None}[which]
         if nnz is None:
             rp = np.zeros(rows + 1, dtype=np.int32)
             lib().oracle_export_csr(self._h, C.c_int(l), C.c_int(code), rp.ctypes.data_as(C.c_void_p), None, None)

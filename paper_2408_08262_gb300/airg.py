@@ -39,7 +39,8 @@ class _Params(C.Structure):
                 ("poly_order", C.c_int), ("coarse_poly_order", C.c_int), ("coarse_iters", C.c_int),
                 ("coarse_size", C.c_int), ("max_levels", C.c_int), ("drop_R", C.c_double), ("drop_Ac", C.c_double),
                 ("n_smooth_up", C.c_int), ("precision", C.c_int), ("keep_setup", C.c_int), ("seed", C.c_uint64),
-                ("sparsity_order", C.c_int)]
+                ("sparsity_order", C.c_int), ("matrix_free", C.c_int),
+                ("ideal_prolong", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -120,6 +121,8 @@ class Params:
     keep_setup: int = 0
     seed: int = 240808262
     sparsity_order: int = 1
+    matrix_free: int = 0
+    ideal_prolong: int = 0
 
     def c(self) -> _Params:
         return _Params(**{k: getattr(self, k) for k, _ in _Params._fields_})
@@ -176,7 +179,7 @@ class Hierarchy:
         return lib().airg_num_levels(self._h)
 
     def level_info(self, level: int) -> dict:
-        info = np.zeros(16, dtype=np.int64)
+        info = np.zeros(17, dtype=np.int64)
         _check(lib().airg_level_info(self._h, level, info.ctypes.data), "airg_level_info")
         if level == -1:
             return dict(levels=int(info[0]), grid=info[1] / 1e6, operator=info[2] / 1e6, storage=info[3] / 1e6,
@@ -184,7 +187,7 @@ class Hierarchy:
                         phase_ms=dict(cf_split=info[5] / 1e3, extract=info[6] / 1e3, polynomial=info[7] / 1e3,
                                       restrictor=info[8] / 1e3, coarse=info[9] / 1e3, layout=info[10] / 1e3))
         keys = ["n", "nnz", "nf", "nc", "nnz_aff", "nnz_afc", "nnz_ainv", "nnz_z", "coarsest", "nnz_acf",
-                "alpha_fitted", "nnz_af", "us_cf", "us_poly", "us_z", "us_coarse"]
+                "alpha_fitted", "nnz_af", "us_cf", "us_poly", "us_z", "us_coarse", "nnz_w"]
         return {k: int(v) for k, v in zip(keys, info)}
 
     def solve(self, b, x=None, outer: str = "fgmres", restart: int = 30, max_it: int = 200, rtol: float = 1e-10,
@@ -221,18 +224,20 @@ class Hierarchy:
 
     def export(self, level: int, which: str):
         """which: A, Aff, Afc, Acf, Ainv, Z (natural numbering, needs keep_setup) or the solve layout
-        AF_solve, Z_solve, A0_solve, Ainv_solve, A_coarsest."""
+        AF_solve, Z_solve, A0_solve, Ainv_solve, A_coarsest; W (natural, keep_setup) and W_solve with
+        ideal_prolong."""
         code = {"A": 0, "Aff": 1, "Afc": 2, "Acf": 3, "Ainv": 5, "Z": 6, "AF_solve": 7, "Z_solve": 8,
-                "A0_solve": 9, "Ainv_solve": 10, "A_coarsest": 11}[which]
+                "A0_solve": 9, "Ainv_solve": 10, "A_coarsest": 11, "W": 12, "W_solve": 13}[which]
         inf = self.level_info(level)
         top = self.level_info(0)
         rows = {"A": inf["n"], "Aff": inf["nf"], "Afc": inf["nf"], "Acf": inf["nc"], "Z": inf["nc"],
                 "Ainv": inf["n"] if inf["coarsest"] else inf["nf"], "AF_solve": inf["nf"], "Z_solve": inf["nc"],
                 "A0_solve": top["n"], "Ainv_solve": inf["n"] if inf["coarsest"] else inf["nf"],
-                "A_coarsest": inf["n"]}[which]
+                "A_coarsest": inf["n"], "W": inf["nf"], "W_solve": inf["nf"]}[which]
         nnz = {"A": inf["nnz"], "Aff": inf["nnz_aff"], "Afc": inf["nnz_afc"], "Acf": inf["nnz_acf"],
                "Z": inf["nnz_z"], "Ainv": inf["nnz_ainv"], "AF_solve": inf["nnz_af"], "Z_solve": inf["nnz_z"],
-               "A0_solve": top["nnz"], "Ainv_solve": inf["nnz_ainv"], "A_coarsest": inf["nnz"]}[which]
+               "A0_solve": top["nnz"], "Ainv_solve": inf["nnz_ainv"], "A_coarsest": inf["nnz"],
+               "W": inf["nnz_w"], "W_solve": inf["nnz_w"]}[which]
         rp = np.zeros(rows + 1, dtype=np.int32)
         ci = np.zeros(nnz, dtype=np.int32)
         v = np.zeros(nnz, dtype=np.float64)

@@ -33,6 +33,7 @@ SetupParams to_setup(const airg_params& p) {
   q.n_smooth_up = p.n_smooth_up;
   q.seed = p.seed;
   q.sparsity_order = p.sparsity_order;
+  q.ideal_prolong = p.ideal_prolong;
   return q;
 }
 
@@ -45,6 +46,10 @@ int check_params(const airg_params* p) {
   if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
   if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
   if (p->sparsity_order != 1 && p->sparsity_order != 2) return AIRG_ERR_ARG;
+  if (p->matrix_free != 0 && p->matrix_free != 1) return AIRG_ERR_ARG;
+  if (p->matrix_free && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
+  if (p->ideal_prolong != 0 && p->ideal_prolong != 1) return AIRG_ERR_ARG;
+  if (p->ideal_prolong && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
   return AIRG_OK;
 }
 
@@ -81,6 +86,20 @@ int copy_csr(const DCsr& A, DCsr& B, Arena& a, cudaStream_t s) {
 }
 
 double avg_len(const DCsr& A) { return A.nrows > 0 ? (double)A.nnz / A.nrows : 1.0; }
+
+// Matrix-free form: the level's coefficients (and A_ff, off the coarsest level) in solve memory.
+static int keep_polynomial(const LevelBuild& L, SolveLevel& S, Arena& a, cudaStream_t s) {
+  S.m = L.m;
+  if (L.m > 0) {
+    AIRG_TRY(a.alloc(&S.alpha, L.m));
+    CU_TRY(cudaMemcpyAsync(S.alpha, L.alpha, sizeof(double) * (size_t)L.m, cudaMemcpyDeviceToDevice, s));
+  }
+  if (!L.coarsest) {
+    AIRG_TRY(copy_csr(L.Aff, S.Aff, a, s));
+    S.lanes_Aff = pick_lanes(avg_len(S.Aff));
+  }
+  return AIRG_OK;
+}
 
 int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
   cudaStream_t s = H->s;
@@ -179,16 +198,19 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
       AIRG_TRY(copy_csr(L.Ainv, S.Ainv, H->solve_mem, s));
       S.lanes_A = pick_lanes(avg_len(S.A));
       S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
+      if (H->p.matrix_free) AIRG_TRY(keep_polynomial(L, S, H->solve_mem, s));
       break;
     }
     S.nf = L.nf;
     S.nc = L.nc;
     const int* lay_next = (l + 1 < nl - 1) ? H->lv[l + 1].lay : nullptr;
-    AIRG_TRY(build_solve_ops(L, lay_next, S.AF, S.Z, &S.w, H->solve_mem, tmp, s));
+    AIRG_TRY(build_solve_ops(L, lay_next, S.AF, S.Z, &S.w, S.W, H->solve_mem, tmp, s));
+    if (S.W.nrows > 0) S.lanes_W = pick_lanes(avg_len(S.W));
     AIRG_TRY(copy_csr(L.Ainv, S.Ainv, H->solve_mem, s));
     S.lanes_AF = pick_lanes(avg_len(S.AF));
     S.lanes_Ainv = pick_lanes(avg_len(S.Ainv));
     S.lanes_Z = pick_lanes(avg_len(S.Z));
+    if (H->p.matrix_free) AIRG_TRY(keep_polynomial(L, S, H->solve_mem, s));
     off += L.nf;
   }
   // top-level operator in the nested solve numbering of level 0
@@ -219,8 +241,12 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     const LevelBuild& L = H->lb[l];
     gs += L.n;
     os += L.A.nnz;
-    if (L.coarsest) st += L.Ainv.nnz + (H->p.coarse_iters > 1 ? L.A.nnz : 0);
-    else st += (double)L.Ainv.nnz + L.Aff.nnz + L.Afc.nnz + (L.Z.nnz + (double)L.nc) + ((double)L.nc + L.nf);
+    // the matrix-free form stores no inverse: its polynomials reuse A_ff and the coarsest A
+    const double inv = H->p.matrix_free ? 0.0 : (double)L.Ainv.nnz;
+    if (L.coarsest) st += inv + ((H->p.coarse_iters > 1 || H->p.matrix_free) ? L.A.nnz : 0);
+    else
+      st += inv + L.Aff.nnz + L.Afc.nnz + (L.Z.nnz + (double)L.nc) +
+            ((double)L.nc + (L.W.nrows > 0 ? (double)L.W.nnz : (double)L.nf));
   }
   // the prolongator count above is an upper bound (F rows without a C neighbour have no entry)
   H->grid_cx = H->n0 > 0 ? gs / H->n0 : 0;
@@ -256,7 +282,7 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
       L.A.rp = L.A.ci = nullptr; L.A.v = nullptr;
       L.cf = nullptr; L.pos = L.Fnat = L.Cnat = nullptr; L.w = nullptr;
       L.Aff.rp = L.Aff.ci = nullptr; L.Afc.rp = L.Afc.ci = nullptr; L.Acf.rp = L.Acf.ci = nullptr;
-      L.Z.rp = L.Z.ci = nullptr; L.Ainv.rp = L.Ainv.ci = nullptr;
+      L.Z.rp = L.Z.ci = nullptr; L.Ainv.rp = L.Ainv.ci = nullptr; L.W.rp = L.W.ci = nullptr; L.W.v = nullptr;
       L.Aff.v = L.Afc.v = L.Acf.v = L.Z.v = L.Ainv.v = nullptr;
       L.alpha = nullptr;
       L.fitted_dev = nullptr;
@@ -309,6 +335,8 @@ void airg_params_default(airg_params* p) {
   p->keep_setup = 0;
   p->seed = 240808262ULL;
   p->sparsity_order = 1;
+  p->matrix_free = 0;
+  p->ideal_prolong = 0;
 }
 
 int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
@@ -458,6 +486,7 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
   info[9] = L.Acf.nnz;
   info[10] = L.fitted;
   info[11] = S.AF.nnz;
+  info[16] = L.W.nnz;
   if (level < (int)H->phase_ms.size())
   {
     const auto& ph = H->phase_ms[level];
@@ -471,7 +500,7 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
 
 int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowptr, int32_t* col, double* val) {
   if (!H || level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
-  if (which < 7 && !H->kept) return AIRG_ERR_ARG;
+  if ((which < 7 || which == 12) && !H->kept) return AIRG_ERR_ARG;
   const LevelBuild& L = H->lb[level];
   const SolveLevel& S = H->lv[level];
   const DCsr* M = nullptr;
@@ -481,6 +510,8 @@ int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowp
     case 9: M = &H->A0s; break;
     case 10: M = &S.Ainv; break;
     case 11: M = &S.A; break;
+    case 12: M = &L.W; break;
+    case 13: M = &S.W; break;
     case 0: M = &L.A; break;
     case 1: M = &L.Aff; break;
     case 2: M = &L.Afc; break;
@@ -490,6 +521,7 @@ int airg_export_csr(const airg_hierarchy* H, int level, int which, int32_t* rowp
     default: return AIRG_ERR_ARG;
   }
   if (L.coarsest && which != 0 && which != 5 && which != 9 && which != 10 && which != 11) return AIRG_ERR_ARG;
+  if ((which == 12 || which == 13) && M->nrows == 0) return AIRG_ERR_ARG;  // one-point level: no W
   if (!L.coarsest && which == 11) return AIRG_ERR_ARG;
   cudaStream_t s = H->s;
   if (rowptr) CU_TRY(cudaMemcpyAsync(rowptr, M->rp, sizeof(int) * ((size_t)M->nrows + 1), cudaMemcpyDeviceToHost, s));
@@ -537,6 +569,13 @@ int airg_profile_enable(airg_hierarchy* H, int enable) {
       if (!S.coarsest) {
         S.bytes_AF = spmv_bytes(S.AF, true, vb, xb);
         S.bytes_Z = spmv_bytes(S.Z, true, vb, xb);
+        if (S.W.nrows > 0) S.bytes_W = spmv_bytes(S.W, false, vb, xb);
+      }
+      if (H->p.matrix_free) {
+        // m - 1 SpMVs that read r in their epilogue, y = alpha r, and x += y
+        const DCsr& M = S.coarsest ? S.A : S.Aff;
+        const double n = M.nrows;
+        S.bytes_mf = S.m > 1 ? (S.m - 1) * spmv_bytes(M, true) + 16.0 * n + 24.0 * n : 24.0 * n;
       }
     }
     H->bytes_A0 = spmv_bytes(H->A0s, false);

@@ -487,6 +487,8 @@ int airg_batch_create(airg_hierarchy* const* Hs, int nsys, airg_stream_t stream,
   for (int q = 0; q < nsys; ++q) {
     if (!Hs[q] || Hs[q]->vt != 0) return AIRG_ERR_ARG;  // FP64 hierarchies
     if (Hs[q]->p.coarse_iters != Hs[0]->p.coarse_iters || Hs[q]->p.n_smooth_up != Hs[0]->p.n_smooth_up) return AIRG_ERR_ARG;
+    // the batched V-cycle applies assembled inverses and one-point prolongators
+    if (Hs[q]->p.matrix_free || Hs[q]->p.ideal_prolong) return AIRG_ERR_ARG;
   }
   airg_batch* B = new (std::nothrow) airg_batch;
   if (!B) return AIRG_ERR_OOM;

@@ -141,9 +141,15 @@ int dev_gs_pass(const double* V, long long ldv, int ncols, double* w, int n, con
 int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, double* x, int n, cudaStream_t s);
 
 // SpMV epilogues
-enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_ADDB = 3 };
+enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_ADDB = 3, SPMV_AXPB = 4 };
 // y = A x (SET) | b - A x (RESID) | y + A x (ADD) | b + A x (ADDB; y may alias b)
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s);
+// y = coef[0] r, or y += coef[0] r with add (coef on the device); x += y
+void dev_coef_axpy(const double* coef, const double* r, double* y, int n, bool add, cudaStream_t s);
+void dev_add(const double* y, double* x, int n, cudaStream_t s);
+// y = coef[0] b + A x, coef a device scalar
+int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double* coef, double* y, int lanes,
+                  cudaStream_t s);
 int pick_lanes(double avg_row_len);
 // r = b_F - AF x with x_F taken as the one-point prolongation of x_C (x[f] = x[nf + w[f]]), which
 // is also stored into x_F.  AF has nf rows; x holds [x_F, x_C].
@@ -171,6 +177,7 @@ struct SetupParams {
   int pmisr_max_loops, poly_order, coarse_poly_order, coarse_iters, coarse_size, max_levels, n_smooth_up;
   uint64_t seed;
   int sparsity_order = 1;  // fixed sparsity of the A_ff polynomials: 1 pattern(A_ff), 2 pattern(A_ff^2)
+  int ideal_prolong = 0;   // 1: P = [W; I] with W = -Ainv A_fc (drop_R), else one-point
 };
 
 // CF splitting of A (natural numbering); cf: device int8 n (1 F, 2 C).  strong (device uint8 nnz)
@@ -216,6 +223,7 @@ struct LevelBuild {
   int* Fnat = nullptr;  // F index -> natural
   int* Cnat = nullptr;  // C index -> natural
   DCsr Aff, Afc, Acf, Ainv, Z;
+  DCsr W;               // approximate ideal prolongator (n_f x n_c, natural C numbering); empty for one-point
   int* w = nullptr;     // F index -> C index (natural C numbering), -1 none
   double* alpha = nullptr;
   int m = 0, fitted = 0;
@@ -244,7 +252,7 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
 // nested numbering (nullptr when the next level is the coarsest: identity there).
 int compose_layout(const LevelBuild& L, const int* lay_next, int* lay, cudaStream_t s);
 // Solve-phase operators of level l given level l+1's nested numbering (nullptr: identity).
-int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, Arena& own,
+int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, DCsr& Ws, Arena& own,
                     Arena& tmp, cudaStream_t s);
 // Symmetric permutation of A by pos: row pos[i] gets row i with columns pos[j].
 int permute_matrix(const DCsr& A, const int* pos, DCsr& out, Arena& own, Arena& tmp, cudaStream_t s);

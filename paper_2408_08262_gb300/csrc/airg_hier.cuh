@@ -21,6 +21,17 @@ struct SolveLevel {
   // mixed precision: the same operators with float or bf16 values (nullptr in FP64 mode)
   void *lo_AF = nullptr, *lo_Ainv = nullptr, *lo_Z = nullptr, *lo_A = nullptr;
   double bytes_AF = 0, bytes_Ainv = 0, bytes_Z = 0, bytes_A = 0;  // algorithmic bytes per SpMV
+  // matrix-free polynomial application: A_ff (non-coarsest levels, F numbering) and the m
+  // coefficients on the device; the coarsest level applies its polynomial with A
+  DCsr Aff;
+  // approximate ideal prolongator (rows n_f, columns in the next level's numbering); empty for
+  // the one-point operator w
+  DCsr W;
+  int lanes_W = 4;
+  double bytes_W = 0;
+  double* alpha = nullptr;
+  int m = 0, lanes_Aff = 4;
+  double bytes_mf = 0;  // algorithmic bytes of one matrix-free application
 };
 
 enum ProfClass { PC_SMOOTH_RESID = 0, PC_SMOOTH_UPDATE, PC_RESTRICT, PC_TOP_OP, PC_COARSEST, PC_PROLONG, PC_GS, PC_N };
@@ -70,6 +81,7 @@ struct airg_hierarchy {
   int restart_alloc = 0;
   double *V = nullptr, *Zk = nullptr, *w = nullptr, *r = nullptr, *bwork = nullptr, *rtmp = nullptr,
          *bp = nullptr, *xp = nullptr, *dsc = nullptr, *hb = nullptr, *hx = nullptr;
+  double *mf_y = nullptr, *mf_y2 = nullptr;  // Horner iterates of the matrix-free polynomial
   double* hsc = nullptr;  // pinned host mirror of dsc
   airg::Reducer red{};
   airg::Profiler prof;

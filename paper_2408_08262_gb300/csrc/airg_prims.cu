@@ -353,7 +353,7 @@ __device__ __forceinline__ float vfma<__nv_bfloat16, float>(__nv_bfloat16 a, flo
 template <typename VT, typename XT, int MODE, bool PROLONG, int kRowBatch>
 __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
-                                                  const int* __restrict__ w, XT* xf) {
+                                                  const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
   for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < nrows; rr += (long long)gridDim.x * blockDim.x) {
     const int row = (int)rr;
     const int rb = rp[row], re = rp[row + 1];
@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
     if (MODE == SPMV_SET) out = s;
     else if (MODE == SPMV_RESID) out = b[row] - s;
     else if (MODE == SPMV_ADD) out = y[row] + s;
+    else if (MODE == SPMV_AXPB) out = coef[0] * b[row] + s;
     else out = b[row] + s;
     y[row] = out;
     if (PROLONG) {
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
 template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
 __global__ void __launch_bounds__(256) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
-                                                  const int* __restrict__ w, XT* xf) {
+                                                  const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
   constexpr int GPW = 32 / LPR;  // rows per warp and pass
   const int lane = threadIdx.x % LPR, grp = (threadIdx.x & 31) / LPR;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int nrows, const int* __restri
       if (MODE == SPMV_SET) out = s;
       else if (MODE == SPMV_RESID) out = b[row] - s;
       else if (MODE == SPMV_ADD) out = y[row] + s;
+      else if (MODE == SPMV_AXPB) out = coef[0] * b[row] + s;
       else out = b[row] + s;
       y[row] = out;
       if (PROLONG) {
@@ -459,56 +461,68 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int nrows, const int* __restri
 
 template <typename VT, typename XT, int RB>
 static void launch_spmv_row(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y,
-                            int mode, const int* w, XT* xf, cudaStream_t s) {
+                            int mode, const int* w, XT* xf, cudaStream_t s, const XT* coef) {
   const int g1 = ceil_div(nrows, 256);
   if (w) {
-    airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
+    airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_AXPB: airg::note_launch(), k_spmv_row<VT, XT, SPMV_AXPB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
   }
 }
 
 template <typename VT, typename XT, int LPR>
 static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                        const int* w, XT* xf, cudaStream_t s, int rb) {
+                        const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef) {
   if constexpr (LPR == 1) {
-    if (rb == 8) launch_spmv_row<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s);
-    else launch_spmv_row<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s);
+    if (rb == 8) launch_spmv_row<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef);
+    else launch_spmv_row<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef);
     return;
   }
   const int grid = ceil_div(nrows, kSpmvThreads / LPR);
   if (w) {
-    airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf);
+    airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
-    default: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr); break;
+    case SPMV_SET: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_AXPB: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_AXPB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    default: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
   }
 }
 
 template <typename VT, typename XT>
 static void spmv_dispatch(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                          int lanes, const int* w, XT* xf, cudaStream_t s, int rb) {
+                          int lanes, const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef = nullptr) {
   switch (lanes) {
-    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
-    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
-    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
-    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
-    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
-    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb); break;
+    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
   }
 }
 
 // Entries loaded per batch by the row-per-thread SpMV: 8 unless the rows average about 4 or fewer.
 static int row_batch(const DCsr& A) { return (double)A.nnz > 4.5 * (double)A.nrows ? 8 : 4; }
+
+// y = coef[0] b + A x (coef on the device): one Horner step of a matrix-free polynomial.
+int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double* coef, double* y, int lanes,
+                  cudaStream_t s) {
+  if (A.nrows <= 0) return AIRG_OK;
+  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, SPMV_AXPB, lanes, nullptr, nullptr, s, row_batch(A),
+                                coef);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
 
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
@@ -616,6 +630,26 @@ __global__ void k_gather_prolong(double* x, int nf, const int* __restrict__ w) {
 }
 void dev_gather_prolong(double* x, int nf, const int* w, cudaStream_t s) {
   if (nf > 0) airg::note_launch(), k_gather_prolong<<<grid_for(nf, 256), 256, 0, s>>>(x, nf, w);
+}
+
+// y = coef[0] r (add = false) or y += coef[0] r (add = true), coef on the device
+__global__ void k_coef_axpy(const double* __restrict__ coef, const double* __restrict__ r, double* __restrict__ y, int n,
+                            bool add) {
+  const double a = coef[0];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = add ? y[i] + a * r[i] : a * r[i];
+}
+void dev_coef_axpy(const double* coef, const double* r, double* y, int n, bool add, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_coef_axpy<<<grid_for(n, 256), 256, 0, s>>>(coef, r, y, n, add);
+}
+
+// x += y
+__global__ void k_add(const double* __restrict__ y, double* __restrict__ x, int n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += y[i];
+}
+void dev_add(const double* y, double* x, int n, cudaStream_t s) {
+  if (n > 0) airg::note_launch(), k_add<<<grid_for(n, 256), 256, 0, s>>>(y, x, n);
 }
 
 __global__ void k_fill(double* x, double v, int n) {

@@ -1775,6 +1775,27 @@ __global__ void k_P_fill(int n, const int8_t* __restrict__ cf, const int* __rest
     if (c >= 0) { ci[rp[i]] = c; v[rp[i]] = 1.0; }
   }
 }
+// Approximate ideal P = [W; I] in natural row numbering: an F row is W's row, a C row the unit
+// entry of its C index.
+__global__ void k_Pw_count(int n, const int8_t* __restrict__ cf, const int* __restrict__ fpos, const int* __restrict__ wrp,
+                           int* __restrict__ cnt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    cnt[i] = (cf[i] == kF) ? wrp[fpos[i] + 1] - wrp[fpos[i]] : 1;
+}
+__global__ void k_Pw_fill(int n, const int8_t* __restrict__ cf, const int* __restrict__ fpos, DCsr W,
+                          const int* __restrict__ rp, int* __restrict__ ci, double* __restrict__ v) {
+  for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)ii;
+    int o = rp[i];
+    if (cf[i] == kF) {
+      const int f = fpos[i];
+      for (int k = W.rp[f]; k < W.rp[f + 1]; ++k) { ci[o] = W.ci[k]; v[o++] = W.v[k]; }
+    } else {
+      ci[o] = i - fpos[i];
+      v[o] = 1.0;
+    }
+  }
+}
 // R = [Z I] in natural column numbering: row c = Z row c (columns Fnat[f]) merged with (Cnat[c], 1).
 __global__ void k_R_fill(int nc, const int* __restrict__ zrp, const int* __restrict__ zci, const double* __restrict__ zv,
                          const int* __restrict__ Fnat, const int* __restrict__ Cnat, int* __restrict__ rrp,
@@ -1892,26 +1913,44 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
   }
   airg::note_launch(), k_one_point<<<grid_for(n, 256), 256, 0, s2>>>(n, A.rp, A.ci, A.v, strong, L.cf, fpos, L.w);
   KERNEL_CHECK();
-  DCsr P;
-  P.nrows = n; P.ncols = nc;
-  int* pc;
-  AIRG_TRY(tmp2->alloc(&pc, n));
-  AIRG_TRY(tmp2->alloc(&P.rp, (size_t)n + 1));
-  airg::note_launch(), k_P_count<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, pc);
-  AIRG_TRY(scan_i32(pc, P.rp, n, *tmp2, s2, nullptr));
-  P.nnz = n;  // upper bound (only P.rp delimits rows); avoids a synchronisation
-  AIRG_TRY(tmp2->alloc(&P.ci, n));
-  AIRG_TRY(tmp2->alloc(&P.v, n));
-  airg::note_launch(), k_P_fill<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
-  KERNEL_CHECK();
   // A P stays in the padded form of the product (no compaction): R reads its rows in place
   SpgPadded AP;
-  AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, *tmp2, s2));
+  if (!p.ideal_prolong) {
+    DCsr P;
+    P.nrows = n; P.ncols = nc;
+    int* pc;
+    AIRG_TRY(tmp2->alloc(&pc, n));
+    AIRG_TRY(tmp2->alloc(&P.rp, (size_t)n + 1));
+    airg::note_launch(), k_P_count<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, pc);
+    AIRG_TRY(scan_i32(pc, P.rp, n, *tmp2, s2, nullptr));
+    P.nnz = n;  // upper bound (only P.rp delimits rows); avoids a synchronisation
+    AIRG_TRY(tmp2->alloc(&P.ci, n));
+    AIRG_TRY(tmp2->alloc(&P.v, n));
+    airg::note_launch(), k_P_fill<<<grid_for(n, 256), 256, 0, s2>>>(n, L.cf, fpos, L.w, P.rp, P.ci, P.v);
+    KERNEL_CHECK();
+    AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, *tmp2, s2));
+  }
   if (s2 != s) CU_TRY(cudaEventRecord(side->join, s2));
   mark(3);
   // step 9
   AIRG_TRY(spgemm(L.Acf, L.Ainv, -1.0, p.drop_R, false, L.Z, own, tmp, s));
   mark(4);
+  // step 10's alternative (eq. prolong): W = -Ainv A_fc with Z's drop, then P = [W; I] and A P
+  if (p.ideal_prolong) {
+    AIRG_TRY(spgemm(L.Ainv, L.Afc, -1.0, p.drop_R, false, L.W, own, tmp, s));
+    DCsr P;
+    P.nrows = n; P.ncols = nc; P.nnz = L.W.nnz + nc;
+    int* pc;
+    AIRG_TRY(tmp.alloc(&pc, n));
+    AIRG_TRY(tmp.alloc(&P.rp, (size_t)n + 1));
+    AIRG_TRY(tmp.alloc(&P.ci, std::max(P.nnz, 1)));
+    AIRG_TRY(tmp.alloc(&P.v, std::max(P.nnz, 1)));
+    airg::note_launch(), k_Pw_count<<<grid_for(n, 256), 256, 0, s>>>(n, L.cf, fpos, L.W.rp, pc);
+    AIRG_TRY(scan_i32(pc, P.rp, n, tmp, s, nullptr));
+    airg::note_launch(), k_Pw_fill<<<grid_for(n, 256), 256, 0, s>>>(n, L.cf, fpos, L.W, P.rp, P.ci, P.v);
+    KERNEL_CHECK();
+    AIRG_TRY(spgemm_padded(A, &P, nullptr, 1.0, 0.0, false, AP, tmp, s));
+  }
   // step 11b: A_c = R (A P)
   DCsr R;
   R.nrows = nc; R.ncols = n; R.nnz = L.Z.nnz + nc;
@@ -1994,7 +2033,7 @@ int compose_layout(const LevelBuild& L, const int* lay_next, int* lay, cudaStrea
   return AIRG_OK;
 }
 
-int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, Arena& own,
+int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs, int** ws, DCsr& Ws, Arena& own,
                     Arena& tmp, cudaStream_t s) {
   const int nf = L.nf, nc = L.nc;
   AIRG_TRY(own.csr(AF, nf, nf + nc, L.Aff.nnz + L.Afc.nnz));
@@ -2009,6 +2048,16 @@ int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs
   AIRG_TRY(own.alloc(ws, std::max(nf, 1)));
   if (nf > 0) airg::note_launch(), k_w_solve<<<GRID(nf)>>>(nf, L.w, pos_next, *ws);
   KERNEL_CHECK();
+  // approximate ideal W: the same rows, columns in the next level's numbering
+  if (L.W.nrows > 0) {
+    AIRG_TRY(own.csr(Ws, nf, nc, L.W.nnz));
+    int* wcnt;
+    AIRG_TRY(tmp.alloc(&wcnt, std::max(nf, 1)));
+    airg::note_launch(), k_perm_rows_count<<<GRID(nf)>>>(nf, L.W.rp, nullptr, wcnt);
+    AIRG_TRY(scan_i32(wcnt, Ws.rp, nf, tmp, s, nullptr));
+    airg::note_launch(), k_perm_rows_fill<<<GRID(nf)>>>(nf, L.W.rp, L.W.ci, L.W.v, nullptr, pos_next, Ws.rp, Ws.ci, Ws.v);
+    KERNEL_CHECK();
+  }
   return AIRG_OK;
 }
 

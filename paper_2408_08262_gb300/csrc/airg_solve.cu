@@ -100,6 +100,10 @@ int solve_alloc(airg_hierarchy* H, int restart) {
     AIRG_TRY(a.alloc(&H->r, n));
     AIRG_TRY(a.alloc(&H->bwork, n));
     AIRG_TRY(a.alloc(&H->rtmp, n));
+    if (H->p.matrix_free) {
+      AIRG_TRY(a.alloc(&H->mf_y, n));
+      AIRG_TRY(a.alloc(&H->mf_y2, n));
+    }
     AIRG_TRY(a.alloc(&H->bp, n));
     AIRG_TRY(a.alloc(&H->xp, n));
     AIRG_TRY(a.alloc(&H->dsc, 256));
@@ -114,6 +118,33 @@ int solve_alloc(airg_hierarchy* H, int restart) {
 // V-cycle.  b0: level-0 rhs (solve numbering, not modified); x0: output (n0 entries).  Level l's
 // rhs lives in bwork[off_l, off_l + n_l) for l >= 1; level l's solution in x0[off_l, ...).
 // ------------------------------------------------------------------------------------------
+// Matrix-free polynomial (Section "AIRG": the stationary polynomial applied without assembling
+// it): x = q(A) r, or x += q(A) r with `accumulate`, where q(A) = sum_{k<m} alpha_k A^k, by Horner's
+// rule: y = alpha_{m-1} r, then y = alpha_k r + A y for k = m-2 .. 0 (m - 1 products by A, each
+// one SpMV with the alpha_k r term in its epilogue).  alpha: device, m entries.
+static int poly_apply_mf(airg_hierarchy* H, const DCsr& A, int lanes, const double* alpha, int m, const double* r,
+                         double* x, bool accumulate, cudaStream_t s) {
+  const int n = A.nrows;
+  if (m <= 0) {
+    if (!accumulate) dev_fill(x, 0.0, n, s);
+    return AIRG_OK;
+  }
+  if (m == 1) {
+    dev_coef_axpy(alpha, r, x, n, accumulate, s);
+    return AIRG_OK;
+  }
+  double* buf[2] = {H->mf_y, H->mf_y2};
+  int cur = 0;
+  dev_coef_axpy(alpha + (m - 1), r, buf[cur], n, false, s);
+  for (int k = m - 2; k >= 0; --k) {
+    double* out = (k == 0 && !accumulate) ? x : buf[cur ^ 1];
+    AIRG_TRY(dev_spmv_axpb(A, buf[cur], r, alpha + k, out, lanes, s));
+    cur ^= 1;
+  }
+  if (accumulate) dev_add(buf[cur], x, n, s);
+  return AIRG_OK;
+}
+
 int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
   cudaStream_t s = H->s;
   Profiler& P = H->prof;
@@ -132,17 +163,20 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
     const SolveLevel& S = H->lv[L];
     const double* bl = bptr(L);
     double* xl = x0 + S.off;
+    const bool mf = H->p.matrix_free != 0;
     {
-      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
-      AIRG_TRY(dev_spmv(S.Ainv, bl, nullptr, xl, SPMV_SET, S.lanes_Ainv, s));
+      ProfScope ps(P, s, PC_COARSEST, mf ? S.bytes_mf : S.bytes_Ainv, L);
+      if (mf) AIRG_TRY(poly_apply_mf(H, S.A, S.lanes_A, S.alpha, S.m, bl, xl, false, s));
+      else AIRG_TRY(dev_spmv(S.Ainv, bl, nullptr, xl, SPMV_SET, S.lanes_Ainv, s));
     }
     for (int it = 1; it < H->p.coarse_iters; ++it) {
       {
         ProfScope ps(P, s, PC_COARSEST, S.bytes_A, L);
         AIRG_TRY(dev_spmv(S.A, xl, bl, H->rtmp, SPMV_RESID, S.lanes_A, s));
       }
-      ProfScope ps(P, s, PC_COARSEST, S.bytes_Ainv, L);
-      AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
+      ProfScope ps(P, s, PC_COARSEST, mf ? S.bytes_mf : S.bytes_Ainv, L);
+      if (mf) AIRG_TRY(poly_apply_mf(H, S.A, S.lanes_A, S.alpha, S.m, H->rtmp, xl, true, s));
+      else AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
     }
   }
   // prolongation and up F-point smoothing
@@ -150,18 +184,27 @@ int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
     const SolveLevel& S = H->lv[l];
     const double* bl = bptr(l);
     double* xl = x0 + S.off;
-    if (H->p.n_smooth_up == 0) {
+    const bool ideal = S.W.nrows > 0;
+    if (ideal) {  // x_F = W x_C (approximate ideal prolongator)
+      ProfScope ps(P, s, PC_PROLONG, S.bytes_W, l);
+      AIRG_TRY(dev_spmv(S.W, xl + S.nf, nullptr, xl, SPMV_SET, S.lanes_W, s));
+    } else if (H->p.n_smooth_up == 0) {
       ProfScope ps(P, s, PC_PROLONG, (double)S.nf * 16.0, l);
       dev_gather_prolong(xl, S.nf, S.w, s);
     }
     for (int sm = 0; sm < H->p.n_smooth_up; ++sm) {
       {
-        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF + (sm == 0 ? 12.0 * S.nf : 0.0), l);
-        if (sm == 0) AIRG_TRY(dev_spmv_resid_prolong(S.AF, xl, S.w, bl, H->rtmp, S.lanes_AF, s));
+        ProfScope ps(P, s, PC_SMOOTH_RESID, S.bytes_AF + (sm == 0 && !ideal ? 12.0 * S.nf : 0.0), l);
+        if (sm == 0 && !ideal) AIRG_TRY(dev_spmv_resid_prolong(S.AF, xl, S.w, bl, H->rtmp, S.lanes_AF, s));
         else AIRG_TRY(dev_spmv(S.AF, xl, bl, H->rtmp, SPMV_RESID, S.lanes_AF, s));
       }
-      ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv, l);
-      AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
+      if (H->p.matrix_free) {
+        ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_mf, l);
+        AIRG_TRY(poly_apply_mf(H, S.Aff, S.lanes_Aff, S.alpha, S.m, H->rtmp, xl, true, s));
+      } else {
+        ProfScope ps(P, s, PC_SMOOTH_UPDATE, S.bytes_Ainv, l);
+        AIRG_TRY(dev_spmv(S.Ainv, H->rtmp, nullptr, xl, SPMV_ADD, S.lanes_Ainv, s));
+      }
     }
   }
   KERNEL_CHECK();

@@ -38,7 +38,8 @@ def gpu_params(op: O.Params, keep=1) -> airg.Params:
                        pmisr_max_loops=op.pmisr_max_loops, poly_order=op.poly_order,
                        coarse_poly_order=op.coarse_poly_order, coarse_iters=op.coarse_iters,
                        coarse_size=op.coarse_size, max_levels=op.max_levels, drop_R=op.drop_R, drop_Ac=op.drop_Ac,
-                       n_smooth_up=op.n_smooth_up, keep_setup=keep, seed=op.seed, sparsity_order=op.sparsity_order)
+                       n_smooth_up=op.n_smooth_up, keep_setup=keep, seed=op.seed, sparsity_order=op.sparsity_order,
+                       matrix_free=op.matrix_free, ideal_prolong=op.ideal_prolong)
 
 
 def assert_csr_close(a, b, rtol=1e-10, what=""):
@@ -97,10 +98,11 @@ def test_cf_split_bitexact_on_oracle_coarse_levels():
 # One level of setup on identical input
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mesh,order,sparsity", [(64, 2, 1), (48, 6, 1), (20, 3, 1), (48, 6, 2), (40, 3, 2)])
-def test_level_operators_match_oracle(mesh, order, sparsity):
+@pytest.mark.parametrize("mesh,order,sparsity,ideal", [(64, 2, 1, 0), (48, 6, 1, 0), (20, 3, 1, 0), (48, 6, 2, 0),
+                                                      (40, 3, 2, 0), (48, 6, 1, 1), (40, 3, 2, 1)])
+def test_level_operators_match_oracle(mesh, order, sparsity, ideal):
     p = P.p1_dg_2d(mesh, 0.3, seed=3 + mesh, sigma_uniform=(0.0, 2.0))
-    op = O.Params(poly_order=order, max_levels=2, coarse_size=0, sparsity_order=sparsity)
+    op = O.Params(poly_order=order, max_levels=2, coarse_size=0, sparsity_order=sparsity, ideal_prolong=ideal)
     Ho = O.Hierarchy(p.rowptr, p.col, p.val, op)
     Hg = airg.Hierarchy(*dev(p), gpu_params(op))
     assert Hg.num_levels == Ho.num_levels == 2
@@ -117,6 +119,11 @@ def test_level_operators_match_oracle(mesh, order, sparsity):
             assert np.array_equal(x, y), which
     assert_csr_close(Ho.export(0, "Ainv"), Hg.export(0, "Ainv"), what="Ainv")
     assert_csr_close(Ho.export(0, "Z"), Hg.export(0, "Z"), what="Z")
+    if ideal:
+        assert io["nnz_w"] == ig["nnz_w"] > io["nf"]
+        assert_csr_close(Ho.export(0, "W"), Hg.export(0, "W"), what="W")
+    else:
+        assert ig["nnz_w"] == 0
     assert_csr_close(Ho.export(1, "A"), Hg.export(1, "A"), what="A_c")
     # coarsest-level polynomial on the same coarse matrix
     np.testing.assert_allclose(Hg.vectors(1)["alpha"], Ho.vectors(1)["alpha"], rtol=1e-8)
@@ -254,6 +261,76 @@ def test_second_order_sparsity_solution_matches_oracle(mesh, degree):
     assert ig["status"] == 0 and io["status"] == 0
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
     assert abs(ig["iters"] - io["iters"]) <= 1
+
+
+def test_matrix_free_vcycle_matches_oracle_two_levels():
+    # the polynomials applied matrix-free (Horner's rule on the GPU, the power series in the oracle)
+    p = P.streaming_2d(40)
+    op = O.Params(max_levels=2, coarse_poly_order=3, matrix_free=1)
+    Ho = O.Hierarchy(p.rowptr, p.col, p.val, op)
+    Hg = airg.Hierarchy(*dev(p), gpu_params(op))
+    b = np.random.default_rng(1).standard_normal(p.n)
+    xo = Ho.vcycle(b)
+    xg = Hg.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-11
+    # and it is a different operator from the assembled fixed-sparsity inverse
+    Ha = airg.Hierarchy(*dev(p), gpu_params(O.Params(max_levels=2, coarse_poly_order=3)))
+    xa = Ha.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.linalg.norm(xa - xo) / np.linalg.norm(xo) > 1e-6
+
+
+@pytest.mark.parametrize("mesh,degree,sparsity", [(64, 2, 1), (48, 6, 1), (33, 1, 1), (48, 3, 2)])
+def test_matrix_free_solution_matches_oracle(mesh, degree, sparsity):
+    p = P.streaming_2d(mesh)
+    xo, io, xg, ig, Hg = solve_both(p, O.Params(poly_order=degree, sparsity_order=sparsity, matrix_free=1))
+    assert Hg.num_levels > 2
+    assert ig["status"] == 0 and io["status"] == 0
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    assert abs(ig["iters"] - io["iters"]) <= 1
+
+
+@pytest.mark.parametrize("flag", ["matrix_free", "ideal_prolong"])
+def test_variants_are_fp64_and_unbatched(flag):
+    p = P.streaming_2d(16)
+    with pytest.raises(airg.AirgError):
+        airg.Hierarchy(*dev(p), airg.Params(precision=1, **{flag: 1}))
+    H = airg.Hierarchy(*dev(p), airg.Params(**{flag: 1}))
+    with pytest.raises(airg.AirgError):
+        airg.Batch([H])
+
+
+@pytest.mark.parametrize("mesh,degree,mf", [(64, 2, 0), (48, 6, 0), (33, 3, 1)])
+def test_ideal_prolongator_solution_matches_oracle(mesh, degree, mf):
+    p = P.streaming_2d(mesh)
+    xo, io, xg, ig, Hg = solve_both(p, O.Params(poly_order=degree, ideal_prolong=1, matrix_free=mf))
+    assert Hg.num_levels > 2 and Hg.level_info(0)["nnz_w"] > Hg.level_info(0)["nf"]
+    assert ig["status"] == 0 and io["status"] == 0
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    assert abs(ig["iters"] - io["iters"]) <= 1
+
+
+def test_ideal_prolongator_interpolates_the_exact_f_values_on_gpu():
+    """eq. prolong with exact A_ff^-1 (unit diagonal, strength 0: A_ff = I), no drops, a converged
+    coarse solve and no smoothing: x_C is exact and x_F = W x_C = x*_F - b_F with the ideal W."""
+    import scipy.sparse as sps
+    p = P.streaming_2d(4)
+    A = p.scipy()
+    d = 1.0 / A.diagonal()
+    As = sps.csr_matrix(sps.diags(d) @ A)
+    As.sort_indices()
+    b = d * p.b
+    xs = np.linalg.solve(As.toarray(), b)
+    op = O.Params(strong_threshold=0.0, ddc_fraction=0.0, drop_R=0.0, drop_Ac=0.0, poly_order=0,
+                  max_levels=2, coarse_size=0, coarse_poly_order=8, coarse_iters=200, n_smooth_up=0,
+                  ideal_prolong=1)
+    H = airg.Hierarchy(*dev((As.indptr.astype(np.int32), As.indices.astype(np.int32), As.data)), gpu_params(op))
+    assert H.num_levels == 2
+    v = H.vectors(0)
+    F, Cp = np.flatnonzero(v["cf"] == 1), np.flatnonzero(v["cf"] == 2)
+    x = H.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    sc = np.abs(xs).max()
+    assert np.abs(x[Cp] - xs[Cp]).max() <= 1e-12 * sc
+    assert np.abs(x[F] - (xs[F] - b[F])).max() <= 1e-12 * sc
 
 
 def test_polynomial_order_trend():

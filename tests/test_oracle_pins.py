@@ -466,6 +466,154 @@ def test_ideal_operators_two_level_exact():
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-12
 
 
+def _dense_poly(M, alpha):
+    Q = np.zeros_like(M)
+    Pk = np.eye(M.shape[0])
+    for a in alpha:
+        Q = Q + a * Pk
+        Pk = Pk @ M
+    return Q
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_matrix_free_coarse_solve_is_the_matrix_polynomial(iters):
+    # Section "AIRG": the stationary polynomial q(A) = sum_k alpha_k A^k applied without assembling
+    # it.  A single-level hierarchy is its coarse solve: one iteration gives q(A) b, two give
+    # q b + q (b - A q b), with q built here from dense matrix powers.
+    p = P.streaming_2d(6)
+    A = p.scipy().toarray()
+    par = O.Params(max_levels=1, coarse_poly_order=5, coarse_iters=iters, matrix_free=1)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, par)
+    alpha = H.vectors(0)["alpha"]
+    assert alpha.size == 6 and np.all(alpha[:2] != 0)
+    Q = _dense_poly(A, alpha)
+    b = np.random.default_rng(3).standard_normal(p.n)
+    x = Q @ b
+    if iters == 2:
+        x = x + Q @ (b - A @ x)
+    got = H.vcycle(b)
+    np.testing.assert_allclose(got, x, rtol=1e-11, atol=1e-12 * np.abs(x).max())
+    # the assembled first-order fixed-sparsity inverse truncates the powers: a different operator
+    Ha = O.Hierarchy(p.rowptr, p.col, p.val, O.Params(max_levels=1, coarse_poly_order=5, coarse_iters=iters))
+    assert np.abs(Ha.vcycle(b) - x).max() > 1e-6 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("matrix_free,ideal", [(0, 0), (1, 0), (0, 1)])
+def test_two_level_vcycle_matches_a_dense_restatement(matrix_free, ideal):
+    # Section "Results" V-cycle on two levels, rebuilt densely from the exported operators:
+    # b_c = b_C + Z b_F; coarse iterations x += M_c (b_c - A_c x); prolongation x_F = W x_C (one-point
+    # or approximate ideal W); then n_smooth_up smooths x_F += M_f (b_F - A_ff x_F - A_fc x_C), with
+    # M the assembled inverse or, matrix-free, the dense polynomial in A_ff (A_c on the coarse
+    # level).  With no drop on A_c, the coarse matrix is the dense triple product R A P.
+    p = P.streaming_2d(8)
+    par = O.Params(max_levels=2, coarse_size=0, poly_order=3, coarse_poly_order=4, coarse_iters=2,
+                   drop_Ac=0.0, matrix_free=matrix_free, ideal_prolong=ideal)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, par)
+    assert H.num_levels == 2
+    i0, i1 = H.level_info(0), H.level_info(1)
+    v0, v1 = H.vectors(0), H.vectors(1)
+    F, Cp = np.flatnonzero(v0["cf"] == 1), np.flatnonzero(v0["cf"] == 2)
+    nf, nc = i0["nf"], i0["nc"]
+    Aff = dense(*H.export(0, "Aff"), nf)
+    Afc = dense(*H.export(0, "Afc"), nc)
+    Z = dense(*H.export(0, "Z"), nf)
+    Ac = dense(*H.export(1, "A"), nc)
+    w = v0["w"]
+    if ideal:
+        W = dense(*H.export(0, "W"), nc)
+        assert i0["nnz_w"] > nf  # more than one entry per F row on average
+    else:
+        W = np.zeros((nf, nc))
+        W[np.flatnonzero(w >= 0), w[w >= 0]] = 1.0
+    Pm = np.zeros((p.n, nc))
+    Pm[F], Pm[Cp] = W, np.eye(nc)
+    Rm = np.zeros((nc, p.n))
+    Rm[:, F], Rm[:, Cp] = Z, np.eye(nc)
+    np.testing.assert_allclose(Ac, Rm @ p.scipy().toarray() @ Pm, rtol=0, atol=1e-13 * np.abs(Ac).max())
+    if matrix_free:
+        Mf, Mc = _dense_poly(Aff, v0["alpha"]), _dense_poly(Ac, v1["alpha"])
+    else:
+        Mf, Mc = dense(*H.export(0, "Ainv"), nf), dense(*H.export(1, "Ainv"), nc)
+    b = np.random.default_rng(5).standard_normal(p.n)
+    bF, bC = b[F], b[Cp]
+    bc = bC + Z @ bF
+    xc = np.zeros(nc)
+    for _ in range(par.coarse_iters):
+        xc = xc + Mc @ (bc - Ac @ xc)
+    xF = W @ xc
+    for _ in range(par.n_smooth_up):
+        xF = xF + Mf @ (bF - Aff @ xF - Afc @ xc)
+    x = np.zeros(p.n)
+    x[F], x[Cp] = xF, xc
+    got = H.vcycle(b)
+    np.testing.assert_allclose(got, x, rtol=1e-10, atol=1e-11 * np.abs(x).max())
+
+
+def test_ideal_prolongator_is_minus_ainv_afc_with_the_restrictor_drop():
+    # eq. prolong: W = -A_ff^-1 A_fc with the assembled Ainv, the counterpart of Z = -A_cf Ainv,
+    # sparsified with the same relative row-wise inf-norm drop (entries below drop_R x row max go)
+    p = P.streaming_2d(12)
+    par = O.Params(max_levels=2, coarse_size=0, ideal_prolong=1)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, par)
+    i0 = H.level_info(0)
+    nf, nc = i0["nf"], i0["nc"]
+    ref = -dense(*H.export(0, "Ainv"), nf) @ dense(*H.export(0, "Afc"), nc)
+    thr = par.drop_R * np.abs(ref).max(axis=1, keepdims=True)
+    near = np.abs(np.abs(ref) - thr) <= 1e-9 * thr
+    assert not near[ref != 0].any()  # no entry within rounding of the threshold
+    ref = np.where(np.abs(ref) >= thr, ref, 0.0)
+    got = dense(*H.export(0, "W"), nc)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+    assert (ref != 0).sum() < (np.abs(-dense(*H.export(0, "Ainv"), nf) @ dense(*H.export(0, "Afc"), nc)) > 0).sum()
+
+
+def test_ideal_prolongator_interpolates_the_exact_f_values():
+    # eq. prolong with an exact A_ff^-1 (unit diagonal and strength 0 make A_ff = I, so degree 0 is
+    # exact), no drops and a converged coarse solve: the coarse correction is exact on the C-points
+    # for any P, and with no smoothing the ideal W gives x_F = W x_C = x*_F - A_ff^-1 b_F, where the
+    # one-point operator does not.
+    p = P.streaming_2d(4)
+    A = p.scipy()
+    d = 1.0 / A.diagonal()
+    As = sp.csr_matrix(sp.diags(d) @ A)
+    As.sort_indices()
+    b = d * p.b
+    xs = np.linalg.solve(As.toarray(), b)
+    out = {}
+    for ideal in (0, 1):
+        par = O.Params(strong_threshold=0.0, ddc_fraction=0.0, drop_R=0.0, drop_Ac=0.0, poly_order=0,
+                       max_levels=2, coarse_size=0, coarse_poly_order=8, coarse_iters=200, n_smooth_up=0,
+                       ideal_prolong=ideal)
+        H = O.Hierarchy(As.indptr, As.indices, As.data, par)
+        v = H.vectors(0)
+        F, Cp = np.flatnonzero(v["cf"] == 1), np.flatnonzero(v["cf"] == 2)
+        x = H.vcycle(b)
+        np.testing.assert_allclose(x[Cp], xs[Cp], rtol=1e-12, atol=1e-12 * np.abs(xs).max())
+        out[ideal] = np.abs(x[F] - (xs[F] - b[F])).max() / np.abs(xs).max()
+    assert out[1] < 1e-12
+    assert out[0] > 1e-3
+
+
+def test_ideal_prolongator_solution_matches_dense_lu():
+    p = P.streaming_2d(16)
+    xs = O.dense_solve(p.rowptr, p.col, p.val, p.b)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params(coarse_size=16, ideal_prolong=1))
+    assert H.num_levels > 2
+    x, info = H.solve(p.b, rtol=1e-12, max_it=300)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
+
+
+def test_matrix_free_airg_solution_matches_dense_lu():
+    p = P.streaming_2d(16)
+    xs = O.dense_solve(p.rowptr, p.col, p.val, p.b)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params(coarse_size=16, matrix_free=1))
+    assert H.num_levels > 2
+    x, info = H.solve(p.b, rtol=1e-12, max_it=300)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
+
+
 def test_vcycle_is_linear():
     p = P.streaming_2d(8)
     H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params())
