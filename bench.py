@@ -66,20 +66,30 @@ def job_value(dofs_per_rank: int, steps: int, world: int, seconds: float) -> flo
     return dofs_per_rank * steps * world / seconds
 
 
-def spmv_traffic():
+# top-level SpMV kernels: (ncu summary, source file, the kernel's signature start)
+SPMV_KERNELS = {
+    "k_spmv_sell": ("k_spmv_sell_top_level_2d_p1dg_640.md", "airg_sell.cu",
+                    "__global__ void __launch_bounds__(256) k_spmv_sell("),
+    "k_spmv_row": ("k_spmv_row_top_level_2d_p1dg_640.md", "airg_prims.cu",
+                   "__global__ void __launch_bounds__(256) k_spmv_row("),
+}
+
+
+def spmv_traffic(kernel: str = "k_spmv_sell"):
     """DRAM bytes per top-level SpMV launch from the committed ncu summary, or None when the kernel
     source has changed since that capture (the summary records a hash of the kernel's source)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_spmv_row_top_level_2d_p1dg_640.md")
-    src = os.path.join(ROOT, "paper_2408_08262_gb300", "csrc", "airg_prims.cu")
+    prof_name, src_name, sig = SPMV_KERNELS[kernel]
+    prof = os.path.join(ROOT, "profiles", prof_name)
+    src = os.path.join(ROOT, "paper_2408_08262_gb300", "csrc", src_name)
     try:
         txt = open(prof).read()
         code = open(src).read()
-        a = code.index("__global__ void __launch_bounds__(256) k_spmv_row(")
+        a = code.index(sig)
         b = code.index("\n}\n", a) + 3
         h = hashlib.sha256(code[a:b].encode()).hexdigest()[:16]
         vals = dict(line.split(": ", 1) for line in txt.splitlines() if ": " in line and line.split(": ")[0].strip().isidentifier())
-        if vals.get("k_spmv_row_source_sha256_16", "").strip() != h:
+        if vals.get(f"{kernel}_source_sha256_16", "").strip() != h:
             return None
         return float(vals["traffic_bytes_per_launch_1024"])
     except Exception:
@@ -240,8 +250,8 @@ def main():
     info0, kt0, lv0 = step(profile=True)
     for _ in range(max(0, args.warmup - 1)):
         step()
-    # The roofline kernel is the CSR SpMV (k_spmv_row on the short-row operators, k_spmv_vec on
-    # longer rows), the dominant kernel family of the step.  In the
+    # The roofline kernel is the SpMV (k_spmv_sell on the large short-row operators, k_spmv_row /
+    # k_spmv_vec on the others), the dominant kernel family of the step.  In the
     # timed region its top-level-operator launches (the largest instance, 6.29M rows) are timed
     # with CUDA events; timing every small-level launch inside the V-cycle graph would itself slow
     # the solve.  The warm-up step times every class and is reported in config.
@@ -306,10 +316,14 @@ def main():
     per_launch_bytes = dom["bytes"] / max(1, dom["launches"])
     fam_bytes = sum(kt0[c]["bytes"] for c in all_spmv)
     fam_ms = sum(kt0[c]["ms"] for c in all_spmv)
-    roofline = {"bound": "hbm", "kernel": "k_spmv_row (row-per-thread CSR SpMV), top-level operator launches (A z in FGMRES, 6.29M rows)",
+    top_kernel = "k_spmv_sell" if lv0.get("top_sell") else "k_spmv_row"
+    label = {"k_spmv_sell": "k_spmv_sell (sliced ELL SpMV, one warp per 32-row slice)",
+             "k_spmv_row": "k_spmv_row (row-per-thread CSR SpMV)"}[top_kernel]
+    roofline = {"bound": "hbm", "kernel": f"{label}, top-level operator launches (A z in FGMRES, {p.n / 1e6:.2f}M rows)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                "traffic": (spmv_traffic() if args.mesh == 1024 else None), "algorithmic_bytes_per_launch": per_launch_bytes,
+                "traffic": (spmv_traffic(top_kernel) if args.mesh == 1024 else None),
+                "algorithmic_bytes_per_launch": per_launch_bytes,
                 "traffic_note": "ncu capture of the same kernel on the 640x640 case scaled by the algorithmic bytes",
                 "launches": dom["launches"], "avg_launch_us": 1e3 * dom["ms"] / max(1, dom["launches"]),
                 "k_spmv_all_launches_first_step": {"achieved": fam_bytes / max(fam_ms, 1e-9) / 1e6,

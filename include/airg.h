@@ -206,15 +206,18 @@ void airg_free(airg_hierarchy* H);
 /* Number of levels (>= 1), or a negative error. */
 int airg_num_levels(const airg_hierarchy* H);
 
-/* Per-level sizes into info[0..16] (host, 17 entries): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
+/* Per-level sizes into info[0..17] (host, 18 entries): n, nnz(A), n_f, n_c, nnz(A_ff), nnz(A_fc), nnz(Ainv),
  * nnz(Z), coarsest flag, nnz(A_cf), fitted polynomial coefficients, nnz(AF solve operator), and the
  * level's setup time in microseconds split as in the paper's per-component setup figure:
  * [12] CF splitting + extraction, [13] GMRES polynomial (steps 3-8), [14] restrictor product,
- * [15] prolongator + coarse matrix; [16] nnz(W) of the approximate ideal prolongator (0 for one-point).
+ * [15] prolongator + coarse matrix; [16] nnz(W) of the approximate ideal prolongator (0 for one-point);
+ * [17] which solve operators the SpMVs read in sliced ELL form (bits: 1 [A_ff A_fc], 2 Ainv, 4 Z,
+ * 8 coarsest A, 16 A_ff of the matrix-free form, 32 W); the others are read as CSR.
  * Level -1 gives totals: [0] levels, [1] grid complexity x1e6, [2] operator complexity x1e6,
  * [3] storage complexity x1e6 (eq. mat_store), [4] setup wall ms x1e3, [5..9] summed microseconds of
  * the five phases (CF splitting, extraction, polynomial, restrictor, prolongator + coarse matrix),
- * [10] microseconds spent building the solve-phase layout. */
+ * [10] microseconds spent building the solve-phase layout (sliced ELL copies included), [11] 1 if the
+ * top-level operator is read in sliced ELL form. */
 int airg_level_info(const airg_hierarchy* H, int level, int64_t* info);
 
 /* Copies a level operator to HOST arrays (sizes from airg_level_info).

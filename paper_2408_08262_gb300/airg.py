@@ -179,15 +179,16 @@ class Hierarchy:
         return lib().airg_num_levels(self._h)
 
     def level_info(self, level: int) -> dict:
-        info = np.zeros(17, dtype=np.int64)
+        info = np.zeros(18, dtype=np.int64)
         _check(lib().airg_level_info(self._h, level, info.ctypes.data), "airg_level_info")
         if level == -1:
             return dict(levels=int(info[0]), grid=info[1] / 1e6, operator=info[2] / 1e6, storage=info[3] / 1e6,
                         setup_ms=info[4] / 1e3,
                         phase_ms=dict(cf_split=info[5] / 1e3, extract=info[6] / 1e3, polynomial=info[7] / 1e3,
-                                      restrictor=info[8] / 1e3, coarse=info[9] / 1e3, layout=info[10] / 1e3))
+                                      restrictor=info[8] / 1e3, coarse=info[9] / 1e3, layout=info[10] / 1e3),
+                        top_sell=int(info[11]))
         keys = ["n", "nnz", "nf", "nc", "nnz_aff", "nnz_afc", "nnz_ainv", "nnz_z", "coarsest", "nnz_acf",
-                "alpha_fitted", "nnz_af", "us_cf", "us_poly", "us_z", "us_coarse", "nnz_w"]
+                "alpha_fitted", "nnz_af", "us_cf", "us_poly", "us_z", "us_coarse", "nnz_w", "sell_mask"]
         return {k: int(v) for k, v in zip(keys, info)}
 
     def solve(self, b, x=None, outer: str = "fgmres", restart: int = 30, max_it: int = 200, rtol: float = 1e-10,

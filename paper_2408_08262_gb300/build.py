@@ -9,7 +9,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libairg.so")
-SOURCES = ["airg_prims.cu", "airg_setup.cu", "airg_solve.cu", "airg_api.cu", "airg_noalloc.cu", "airg_adjoint.cu", "airg_batched.cu"]
+SOURCES = ["airg_prims.cu", "airg_setup.cu", "airg_solve.cu", "airg_api.cu", "airg_noalloc.cu", "airg_adjoint.cu", "airg_batched.cu",
+           "airg_sell.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

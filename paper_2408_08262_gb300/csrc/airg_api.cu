@@ -222,6 +222,24 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     H->pos0 = nullptr;
   }
   H->lanes_A0 = pick_lanes(avg_len(H->A0s));
+  // sliced ELL copies of the large short-row FP64 operators whose rows hold about 5 entries or
+  // more: the top-level operator and, when the V-cycle runs in FP64, the smoothing residual's
+  // [A_ff A_fc].  The shorter-row Ainv and Z stay CSR: there the permuted output and the lost
+  // locality of x between a warp's rows cost more than the coalesced loads gain.
+  // AIRG_NO_SELL=1 keeps every SpMV on CSR.
+  if (!getenv("AIRG_NO_SELL")) {
+    auto mk = [&](DCsr& M) -> int {
+      if (!want_sell(M)) return AIRG_OK;
+      H->sells.emplace_back();
+      AIRG_TRY(build_sell(M, H->sells.back(), H->solve_mem, tmp, s));
+      M.sell = &H->sells.back();
+      return AIRG_OK;
+    };
+    AIRG_TRY(mk(H->A0s));
+    if (H->p.precision == AIRG_FP64)
+      for (auto& S : H->lv)
+        if (!S.coarsest) AIRG_TRY(mk(S.AF));
+  }
   if (ev_layout1) cudaEventRecord(ev_layout1, s);
   // mixed-precision form: low-precision copies of every V-cycle operator
   H->vt = H->p.precision == AIRG_FP32 ? 1 : (H->p.precision == AIRG_BF16_VALUES ? 2 : 0);
@@ -469,6 +487,7 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
       for (int k = 0; k < 5; ++k) tot[k] += v[k];
     for (int k = 0; k < 5; ++k) info[5 + k] = (int64_t)std::llround(tot[k] * 1e3);
     info[10] = (int64_t)std::llround(H->layout_ms * 1e3);
+    info[11] = H->A0s.sell ? 1 : 0;
     return AIRG_OK;
   }
   if (level < 0 || level >= (int)H->lb.size()) return AIRG_ERR_ARG;
@@ -487,6 +506,8 @@ int airg_level_info(const airg_hierarchy* H, int level, int64_t* info) {
   info[10] = L.fitted;
   info[11] = S.AF.nnz;
   info[16] = L.W.nnz;
+  info[17] = (S.AF.sell ? 1 : 0) | (S.Ainv.sell ? 2 : 0) | (S.Z.sell ? 4 : 0) | (S.A.sell ? 8 : 0) |
+             (S.Aff.sell ? 16 : 0) | (S.W.sell ? 32 : 0);
   if (level < (int)H->phase_ms.size())
   {
     const auto& ph = H->phase_ms[level];

@@ -33,11 +33,27 @@ constexpr int kF = 1;  // CF marker values (device and export): 0 unassigned, 1 
 constexpr int kC = 2;
 
 // Library-owned device CSR.
+// Sliced ELL copy of a CSR operator for the solve (FP64): rows sorted by length within windows of
+// kSellWindow rows, then cut into slices of 32 rows; slice s holds its rows' entries column-major
+// (entry k of the slice's lane l at sp[s] + 32 k + l), padded to the slice's longest row with
+// column -1.  perm[32 s + l] is the CSR row of that lane (-1 past the last row).  Entries keep their
+// CSR order within a row.
+struct DSell {
+  int nrows = 0, nslices = 0;
+  long long nnz_pad = 0;
+  int* sp = nullptr;
+  int* ci = nullptr;
+  double* v = nullptr;
+  int* perm = nullptr;
+};
+constexpr int kSellWindow = 1024;
+
 struct DCsr {
   int nrows = 0, ncols = 0, nnz = 0;
   int* rp = nullptr;
   int* ci = nullptr;
   double* v = nullptr;
+  const DSell* sell = nullptr;  // optional sliced ELL copy the FP64 SpMVs use instead (solve operators)
 };
 
 // Stream-ordered device memory.  An Arena hands out 256-byte-aligned sub-ranges of large chunks
@@ -144,6 +160,14 @@ int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, d
 enum SpmvMode { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2, SPMV_ADDB = 3, SPMV_AXPB = 4 };
 // y = A x (SET) | b - A x (RESID) | y + A x (ADD) | b + A x (ADDB; y may alias b)
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s);
+// Sliced ELL copies of solve operators (airg_sell.cu).  want_sell: large operators with short rows.
+// build_sell synchronises the stream (the padded size allocates the arrays).  sell_spmv: the same
+// modes and epilogues as the CSR SpMVs (w != nullptr: RESID with the fused one-point prolongation).
+constexpr int kSellMinRows = 32768;
+bool want_sell(const DCsr& A);
+int build_sell(const DCsr& A, DSell& out, Arena& own, Arena& tmp, cudaStream_t s);
+int sell_spmv(const DSell& S, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
+              const double* coef, cudaStream_t s);
 // y = coef[0] r, or y += coef[0] r with add (coef on the device); x += y
 void dev_coef_axpy(const double* coef, const double* r, double* y, int n, bool add, cudaStream_t s);
 void dev_add(const double* y, double* x, int n, cudaStream_t s);

@@ -1,5 +1,6 @@
 // The hierarchy object behind the opaque airg_hierarchy handle.
 #pragma once
+#include <deque>
 #include <vector>
 
 #include "airg_common.cuh"
@@ -74,6 +75,7 @@ struct airg_hierarchy {
   std::vector<airg::SolveLevel> lv;
   int n0 = 0;
   airg::DCsr A0s;  // top-level matrix in level-0 F-then-C numbering
+  std::deque<airg::DSell> sells;  // sliced ELL copies the solve operators point to (DCsr::sell)
   int* pos0 = nullptr;  // natural -> solve numbering (nullptr: identity)
   int lanes_A0 = 4;
   double bytes_A0 = 0;

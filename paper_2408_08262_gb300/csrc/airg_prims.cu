@@ -346,9 +346,42 @@ __device__ __forceinline__ float vfma<__nv_bfloat16, float>(__nv_bfloat16 a, flo
 
 
 
+// Entries k0 .. k0+R-1 of a row (those below re): loads, then gathers of x, then R FMAs in
+// entry order.  R is a compile-time count, so that the FP64 FMAs a warp issues stop at its longest
+// row: on sm_103a the FP64 pipe takes about 64 cycles per warp instruction whether or not its
+// lanes are predicated off, and the SpMVs are close to that pipe's rate.
+template <typename VT, typename XT, bool PROLONG, int R>
+__device__ __forceinline__ XT row_entries(const int* __restrict__ ci, const VT* __restrict__ v, int k0, int re,
+                                          const XT* x, int nrows, const int* __restrict__ w, XT s) {
+  int c[R];
+  VT a[R];
+  XT xv[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    c[t] = (k0 + t < re) ? __ldcs(ci + k0 + t) : -1;
+    a[t] = (k0 + t < re) ? __ldcs(v + k0 + t) : VT(0);
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    xv[t] = XT(0);
+    if (c[t] >= 0) {
+      if (PROLONG && c[t] < nrows) {
+        const int src = w[c[t]];
+        xv[t] = src >= 0 ? x[nrows + src] : XT(0);
+      } else {
+        xv[t] = __ldg(x + c[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t)
+    if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
+  return s;
+}
+
 // Short rows (average <= 12 entries): one thread per row reads its own entries directly, kRowBatch
-// (4 for rows of about 4 entries or fewer, else 8) at a time (the
-// warp's rows are contiguous, so the lines they touch arrive once in L1) and accumulates with one
+// (4 for rows of about 4 entries or fewer, else 8) at a time (the warp's rows are contiguous, so
+// the lines they touch arrive once in L1), up to the warp's longest row, and accumulates with one
 // fused multiply-add per entry, in storage order; no shared memory and no barrier.
 template <typename VT, typename XT, int MODE, bool PROLONG, int kRowBatch>
 __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
@@ -357,31 +390,20 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
   for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < nrows; rr += (long long)gridDim.x * blockDim.x) {
     const int row = (int)rr;
     const int rb = rp[row], re = rp[row + 1];
+    const int wmax = (int)__reduce_max_sync(__activemask(), (unsigned)(re - rb));  // uniform over the lanes here
     XT s = XT(0);
-    for (int k0 = rb; k0 < re; k0 += kRowBatch) {
-      int c[kRowBatch];
-      VT a[kRowBatch];
-      XT xv[kRowBatch];
-#pragma unroll
-      for (int t = 0; t < kRowBatch; ++t) {
-        c[t] = (k0 + t < re) ? __ldcs(ci + k0 + t) : -1;
-        a[t] = (k0 + t < re) ? __ldcs(v + k0 + t) : VT(0);
-      }
-#pragma unroll
-      for (int t = 0; t < kRowBatch; ++t) {
-        xv[t] = XT(0);
-        if (c[t] >= 0) {
-          if (PROLONG && c[t] < nrows) {
-            const int src = w[c[t]];
-            xv[t] = src >= 0 ? x[nrows + src] : XT(0);
-          } else {
-            xv[t] = __ldg(x + c[t]);
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < kRowBatch; ++t)
-        if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
+    int j0 = 0;
+    for (; j0 + kRowBatch <= wmax; j0 += kRowBatch)
+      s = row_entries<VT, XT, PROLONG, kRowBatch>(ci, v, rb + j0, re, x, nrows, w, s);
+    switch (wmax - j0) {
+      case 1: s = row_entries<VT, XT, PROLONG, 1>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 2: s = row_entries<VT, XT, PROLONG, 2>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 3: s = row_entries<VT, XT, PROLONG, 3>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 4: s = row_entries<VT, XT, PROLONG, 4>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 5: s = row_entries<VT, XT, PROLONG, 5>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 6: s = row_entries<VT, XT, PROLONG, 6>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      case 7: s = row_entries<VT, XT, PROLONG, 7>(ci, v, rb + j0, re, x, nrows, w, s); break;
+      default: break;
     }
     XT out;
     if (MODE == SPMV_SET) out = s;
@@ -518,6 +540,7 @@ static int row_batch(const DCsr& A) { return (double)A.nnz > 4.5 * (double)A.nro
 int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double* coef, double* y, int lanes,
                   cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
+  if (A.sell) return sell_spmv(*A.sell, x, b, y, SPMV_AXPB, nullptr, nullptr, coef, s);
   spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, SPMV_AXPB, lanes, nullptr, nullptr, s, row_batch(A),
                                 coef);
   KERNEL_CHECK();
@@ -526,6 +549,7 @@ int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double*
 
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
+  if (A.sell) return sell_spmv(*A.sell, x, b, y, mode, nullptr, nullptr, nullptr, s);
   spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s, row_batch(A));
   KERNEL_CHECK();
   return AIRG_OK;
@@ -535,6 +559,7 @@ int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mod
 int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,
                            cudaStream_t s) {
   if (AF.nrows <= 0) return AIRG_OK;
+  if (AF.sell) return sell_spmv(*AF.sell, x, b, y, SPMV_RESID, w, x, nullptr, s);
   spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s, row_batch(AF));
   KERNEL_CHECK();
   return AIRG_OK;

@@ -1,0 +1,236 @@
+// Sliced ELL (SELL-32-sigma) copies of the solve-phase operators and their SpMV.
+//
+// The solve's operators on the large levels have short rows (the 2D P1 DG top level holds rows of
+// 3, 5 and 7 entries).  In CSR with one thread per row, the 32 lanes of a warp read 32 different
+// rows, so every load instruction of columns and values touches many cache lines and the kernel is
+// limited by L1 wavefronts and load latency rather than by DRAM.  Here the 32 rows of a warp are
+// stored column-major (entry k of the 32 rows side by side), so each load instruction reads one
+// contiguous 128-byte (columns) or 256-byte (values) segment.  Rows are sorted by length inside
+// windows of kSellWindow rows before slicing, which keeps the padding to the slice's longest row
+// near zero (about 1 % on the DG operators).  Each row's entries keep their CSR order and are
+// accumulated with one FMA each from zero, in that order: the result is bitwise the CSR row
+// kernel's.
+#include "airg_common.cuh"
+
+namespace airg {
+
+namespace {
+
+constexpr int kSellBuckets = 64;  // row lengths >= 63 share the last bucket (unsorted among themselves)
+
+// R entries of a slice from k0 on: loads first (R in flight per lane), then the gathers of x, then
+// R FMAs in entry order.  R is a compile-time count so that exactly the slice's width in FP64
+// FMAs is issued: on sm_103a the FP64 pipe takes about 64 cycles per warp instruction, so FMAs
+// issued for entries past the width (predicated off) would cost as much as real ones.
+template <int R, bool PROLONG>
+__device__ __forceinline__ double sell_batch(const int* cs, const double* vs, int k0, const double* x, int nrows,
+                                             const int* __restrict__ w, double s) {
+  int c[R];
+  double a[R], xv[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    c[t] = __ldcs(cs + (k0 + t) * 32);
+    a[t] = __ldcs(vs + (k0 + t) * 32);
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    xv[t] = 0.0;
+    if (c[t] >= 0) {
+      if (PROLONG && c[t] < nrows) {
+        const int src = w[c[t]];
+        xv[t] = src >= 0 ? x[nrows + src] : 0.0;
+      } else {
+        xv[t] = __ldg(x + c[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t)
+    if (c[t] >= 0) s = fma(a[t], xv[t], s);
+  return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// SpMV: one warp per slice (one launch wave after another; a persistent-warp variant that
+// prefetched the next slice's offsets measured 40 % slower), lane l of slice s computes row
+// perm[32 s + l].
+// ------------------------------------------------------------------------------------------
+template <int MODE, bool PROLONG>
+__global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const int* __restrict__ sp,
+                                                   const int* __restrict__ ci, const double* __restrict__ v,
+                                                   const int* __restrict__ perm, const double* x, const double* b,
+                                                   double* y, const int* __restrict__ w, double* xf,
+                                                   const double* __restrict__ coef) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+    const int beg = sp[sl];
+    const int width = (sp[sl + 1] - beg) >> 5;  // warp-uniform
+    const int row = perm[sl * 32 + lane];
+    const int* cs = ci + beg + lane;
+    const double* vs = v + beg + lane;
+    double s = 0.0;
+    int k0 = 0;
+    for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s);
+    switch (width - k0) {  // warp-uniform remainder
+      case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 4: s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 5: s = sell_batch<5, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 6: s = sell_batch<6, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 7: s = sell_batch<7, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      default: break;
+    }
+    if (row >= 0) {
+      double out;
+      if (MODE == SPMV_SET) out = s;
+      else if (MODE == SPMV_RESID) out = b[row] - s;
+      else if (MODE == SPMV_ADD) out = y[row] + s;
+      else if (MODE == SPMV_AXPB) out = coef[0] * b[row] + s;
+      else out = b[row] + s;
+      y[row] = out;
+      if (PROLONG) {
+        const int src = w[row];
+        xf[row] = src >= 0 ? x[nrows + src] : 0.0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Conversion
+// ------------------------------------------------------------------------------------------
+// One block of kSellWindow threads per window: a stable counting sort of the window's rows by
+// descending length bucket.  Lanes of a warp that share a bucket are ranked with a match mask;
+// per-warp bucket counts in shared memory give each warp's offset within a bucket.  Positions past
+// the last row get perm -1 (bucket kSellBuckets, sorted last).
+__global__ void __launch_bounds__(kSellWindow) k_sell_sort(int n, const int* __restrict__ rp, int* __restrict__ perm) {
+  constexpr int NW = kSellWindow / 32, NB = kSellBuckets + 1;
+  __shared__ int cnt[NW][NB];
+  __shared__ int base[NB];
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  for (int i = t; i < NW * NB; i += blockDim.x) cnt[i / NB][i % NB] = 0;
+  __syncthreads();
+  const long long row = (long long)blockIdx.x * kSellWindow + t;
+  int key = kSellBuckets;
+  if (row < n) {
+    const int len = rp[row + 1] - rp[row];
+    key = (kSellBuckets - 1) - min(len, kSellBuckets - 1);  // longer rows first
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (rank == 0) cnt[wp][key] = __popc(peers);
+  __syncthreads();
+  if (t < NB) {  // exclusive scan over warps, per bucket
+    int acc = 0;
+    for (int q = 0; q < NW; ++q) {
+      const int c = cnt[q][t];
+      cnt[q][t] = acc;
+      acc += c;
+    }
+    base[t] = acc;  // bucket total for now
+  }
+  __syncthreads();
+  if (t == 0) {  // exclusive scan over buckets
+    int acc = 0;
+    for (int q = 0; q < NB; ++q) {
+      const int c = base[q];
+      base[q] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  const int pos = base[key] + cnt[wp][key] + rank;
+  perm[(long long)blockIdx.x * kSellWindow + pos] = row < n ? (int)row : -1;
+}
+
+// Entries per slice (32 x its longest row).
+__global__ void k_sell_width(int nslices, const int* __restrict__ rp, const int* __restrict__ perm, int* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+    const int row = perm[sl * 32 + lane];
+    int len = row >= 0 ? rp[row + 1] - rp[row] : 0;
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) cnt[sl] = 32 * len;
+  }
+}
+
+__global__ void k_sell_fill(int nslices, const int* __restrict__ rp, const int* __restrict__ aci,
+                            const double* __restrict__ av, const int* __restrict__ perm, const int* __restrict__ sp,
+                            int* __restrict__ ci, double* __restrict__ v) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
+    const int beg = sp[sl], width = (sp[sl + 1] - beg) >> 5;
+    const int row = perm[sl * 32 + lane];
+    const int rb = row >= 0 ? rp[row] : 0, len = row >= 0 ? rp[row + 1] - rb : 0;
+    for (int k = 0; k < width; ++k) {
+      const bool in = k < len;
+      ci[beg + k * 32 + lane] = in ? aci[rb + k] : -1;
+      v[beg + k * 32 + lane] = in ? av[rb + k] : 0.0;
+    }
+  }
+}
+
+template <int MODE, bool PROLONG>
+void launch_sell(const DSell& S, const double* x, const double* b, double* y, const int* w, double* xf,
+                 const double* coef, cudaStream_t s) {
+  const int grid = ceil_div(S.nslices, 256 / 32);
+  airg::note_launch(), k_spmv_sell<MODE, PROLONG><<<grid, 256, 0, s>>>(S.nslices, S.nrows, S.sp, S.ci, S.v, S.perm, x, b, y,
+                                                                       w, xf, coef);
+}
+
+}  // namespace
+
+bool want_sell(const DCsr& A) {
+  // large operators whose rows the one-thread-per-row kernel would take (short rows)
+  return A.nrows >= kSellMinRows && pick_lanes(A.nrows > 0 ? (double)A.nnz / A.nrows : 1.0) == 1;
+}
+
+int build_sell(const DCsr& A, DSell& out, Arena& own, Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  const int nwin = ceil_div(n, kSellWindow);
+  const int nslices = nwin * (kSellWindow / 32);
+  out.nrows = n;
+  out.nslices = nslices;
+  AIRG_TRY(own.alloc(&out.perm, (size_t)nwin * kSellWindow));
+  AIRG_TRY(own.alloc(&out.sp, (size_t)nslices + 1));
+  int* cnt;
+  AIRG_TRY(tmp.alloc(&cnt, (size_t)nslices));
+  if (nwin > 0) airg::note_launch(), k_sell_sort<<<nwin, kSellWindow, 0, s>>>(n, A.rp, out.perm);
+  KERNEL_CHECK();
+  airg::note_launch(), k_sell_width<<<grid_for((long long)nslices * 32, 256), 256, 0, s>>>(nslices, A.rp, out.perm, cnt);
+  KERNEL_CHECK();
+  long long total = 0;
+  AIRG_TRY(scan_i32(cnt, out.sp, nslices, tmp, s, &total));  // synchronises: total sizes the arrays
+  if (total > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
+  out.nnz_pad = total;
+  AIRG_TRY(own.alloc(&out.ci, (size_t)std::max(total, 1LL)));
+  AIRG_TRY(own.alloc(&out.v, (size_t)std::max(total, 1LL)));
+  airg::note_launch(), k_sell_fill<<<grid_for((long long)nslices * 32, 256), 256, 0, s>>>(nslices, A.rp, A.ci, A.v,
+                                                                                          out.perm, out.sp, out.ci, out.v);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+int sell_spmv(const DSell& S, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
+              const double* coef, cudaStream_t s) {
+  if (S.nslices <= 0) return AIRG_OK;
+  if (w) {
+    launch_sell<SPMV_RESID, true>(S, x, b, y, w, xf, coef, s);
+  } else {
+    switch (mode) {
+      case SPMV_SET: launch_sell<SPMV_SET, false>(S, x, b, y, w, xf, coef, s); break;
+      case SPMV_RESID: launch_sell<SPMV_RESID, false>(S, x, b, y, w, xf, coef, s); break;
+      case SPMV_ADD: launch_sell<SPMV_ADD, false>(S, x, b, y, w, xf, coef, s); break;
+      case SPMV_AXPB: launch_sell<SPMV_AXPB, false>(S, x, b, y, w, xf, coef, s); break;
+      default: launch_sell<SPMV_ADDB, false>(S, x, b, y, w, xf, coef, s); break;
+    }
+  }
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+}  // namespace airg

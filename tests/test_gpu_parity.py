@@ -413,6 +413,25 @@ def test_setup_is_deterministic_run_to_run():
     assert i1 == i2 and torch.equal(x1, x2)
 
 
+@pytest.mark.parametrize("variant", [{}, {"matrix_free": 1}, {"ideal_prolong": 1}])
+def test_sliced_ell_and_csr_solves_agree_bitwise(monkeypatch, variant):
+    # the sliced ELL SpMV keeps each row's CSR entry order and accumulates from zero with one FMA
+    # per entry, as the CSR row kernel does: the solves are bitwise identical
+    p = P.blocked_sigma_2d(160)  # 153,600 rows: the top levels take the sliced form
+    b = torch.from_numpy(p.b).cuda()
+    Hs = airg.Hierarchy(*dev(p), airg.Params(**variant))
+    assert Hs.level_info(-1)["top_sell"] == 1
+    assert Hs.level_info(0)["sell_mask"] & 1  # [A_ff A_fc]
+    xs, is_ = Hs.solve(b, rtol=1e-10)
+    monkeypatch.setenv("AIRG_NO_SELL", "1")
+    Hc = airg.Hierarchy(*dev(p), airg.Params(**variant))
+    assert Hc.level_info(-1)["top_sell"] == 0 and Hc.level_info(0)["sell_mask"] == 0
+    xc, ic = Hc.solve(b, rtol=1e-10)
+    assert is_["status"] == ic["status"] == 0
+    assert is_["iters"] == ic["iters"]
+    assert torch.equal(xs, xc)
+
+
 def test_graph_and_eager_vcycles_agree_bitwise(monkeypatch):
     p = P.blocked_sigma_2d(80)
     b = torch.from_numpy(p.b).cuda()
