@@ -129,6 +129,19 @@ void airg_params_default(airg_params* p);
  * AIRG_ERR_ZERO_DIAG, AIRG_ERR_OOM, AIRG_ERR_CUDA, AIRG_ERR_UNSUPPORTED; *out is NULL then. */
 int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out);
 
+/* Setup re-use (Sections "Strong tolerances" and "Conclusions" name re-using the CF splitting
+ * across the many solves of a Boltzmann problem).  Builds the hierarchy of A as airg_setup does,
+ * except that the CF splittings of the first `levels` levels (levels <= 0: every non-coarsest level
+ * of T) are taken from the template hierarchy T instead of computed (no strength graph transpose,
+ * PMISR or DDC there).  Intended for a matrix with T's sparsity pattern and new values (another
+ * energy group, cross section or time step of the same mesh and direction).  With strength
+ * threshold 0 the level-0 splitting depends on the pattern only, so re-using it reproduces a fresh
+ * setup exactly; deeper levels (whose patterns depend on the drops) get a valid, not identical,
+ * splitting.  T is only read and must stay alive during the call; A->n must equal T's size, else
+ * AIRG_ERR_ARG.  Same parameters, errors and ownership as airg_setup otherwise. */
+int airg_setup_reuse(const airg_csr* A, const airg_params* p, const airg_hierarchy* T, int levels,
+                     airg_stream_t stream, airg_hierarchy** out);
+
 /* Solves A x = b with the hierarchy as preconditioner.  b, x: device, n FP64.  x holds the initial
  * guess on entry (unless opts->x0_zero) and the solution on exit.  Synchronises the stream once per
  * iteration.  Returns AIRG_OK, AIRG_NOT_CONVERGED, or an error (x undefined on error). */

@@ -669,7 +669,10 @@ Csr coarse_matrix(const Level& L, double drop) {
   return spgemm(R, AP, 1.0, drop, true);
 }
 
-void build(Hier& H, const Csr& A0) {
+// forced[l] (when l < forced.size()) is level l's CF splitting, taken as given instead of computed
+// (setup re-use); the strength flags the one-point prolongator reads are still computed.  Returns
+// false if a forced splitting does not have its level's size.
+bool build(Hier& H, const Csr& A0, const std::vector<std::vector<int8_t>>& forced = {}) {
   const Params& p = H.p;
   H.top_nnz = A0.nnz();
   Csr A = A0;
@@ -680,7 +683,14 @@ void build(Hier& H, const Csr& A0) {
     int n = A.nrows;
     bool coarsest = (n <= p.coarse_size) || (n < m) || (l == p.max_levels - 1);
     std::vector<int8_t> strong;
-    if (!coarsest) {
+    if (!coarsest && l < (int)forced.size()) {
+      if ((int)forced[l].size() != n) return false;
+      L.cf = forced[l];
+      L.cf_pmisr = forced[l];
+      strong = strength(A, p.strong_threshold);
+      long nf = std::count(L.cf.begin(), L.cf.end(), (int8_t)F);
+      if (nf == 0 || nf == n) { coarsest = true; L.cf.clear(); L.cf_pmisr.clear(); }
+    } else if (!coarsest) {
       CfDetail d = cf_split(A, p, l);
       L.cf = d.cf;
       L.cf_pmisr = d.cf_pmisr;
@@ -696,7 +706,7 @@ void build(Hier& H, const Csr& A0) {
       L.alpha_fitted = poly_fit(A, mc, bt, L.alpha);
       L.Ainv = fixed_sparsity_inverse(A, L.alpha, 1);
       H.lv.push_back(std::move(L));
-      return;
+      return true;
     }
     extract(L);
     std::vector<double> bt = box_muller(p.seed, l, (int)L.Fnat.size());
@@ -968,6 +978,25 @@ int oracle_setup(int n, const int* rp, const int* ci, const double* v, const dou
   if (!H) return -1;
   H->p = to_params(dp, ip);
   build(*H, make_csr(n, n, rp, ci, v));
+  *out = H;
+  return 0;
+}
+
+// Setup with the CF splittings of the first nforced levels given (cfs[l]: cf_len[l] entries,
+// 1 = F, 2 = C): the setup re-use of the library, restated.  Returns -2 if a splitting does not
+// have its level's size.
+int oracle_setup_forced(int n, const int* rp, const int* ci, const double* v, const double* dp, const long long* ip,
+                        int nforced, const int8_t* const* cfs, const int* cf_len, void** out) {
+  if (!out || !valid_csr(n, rp, ci) || nforced < 0) return -1;
+  std::vector<std::vector<int8_t>> forced(nforced);
+  for (int l = 0; l < nforced; ++l) forced[l].assign(cfs[l], cfs[l] + cf_len[l]);
+  Hier* H = new (std::nothrow) Hier;
+  if (!H) return -1;
+  H->p = to_params(dp, ip);
+  if (!build(*H, make_csr(n, n, rp, ci, v), forced)) {
+    delete H;
+    return -2;
+  }
   *out = H;
   return 0;
 }

@@ -42,6 +42,7 @@ def lib():
         build()
         _lib = C.CDLL(_LIB)
         _lib.oracle_setup.restype = C.c_int
+        _lib.oracle_setup_forced.restype = C.c_int
         _lib.oracle_num_levels.restype = C.c_int
         _lib.oracle_free.restype = None
     return _lib
@@ -84,15 +85,26 @@ def _csr(rowptr, col, val):
 
 
 class Hierarchy:
-    def __init__(self, rowptr, col, val, params: Params | None = None):
+    def __init__(self, rowptr, col, val, params: Params | None = None, cf=None):
+        """cf: optional list of CF splittings (int8 arrays, 1 = F, 2 = C) taken as given for the
+        first len(cf) levels (setup re-use)."""
         self.params = params or Params()
         rp, ci, v = _csr(rowptr, col, val)
         self.n = len(rp) - 1
         dp, ip = self.params.arrays()
         h = C.c_void_p()
-        rc = lib().oracle_setup(C.c_int(self.n), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
-                                v.ctypes.data_as(C.c_void_p), dp.ctypes.data_as(C.c_void_p),
-                                ip.ctypes.data_as(C.c_void_p), C.byref(h))
+        if cf:
+            arrs = [np.ascontiguousarray(c, dtype=np.int8) for c in cf]
+            ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+            lens = np.array([a.size for a in arrs], dtype=np.int32)
+            rc = lib().oracle_setup_forced(C.c_int(self.n), rp.ctypes.data_as(C.c_void_p),
+                                           ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                                           dp.ctypes.data_as(C.c_void_p), ip.ctypes.data_as(C.c_void_p),
+                                           C.c_int(len(arrs)), ptrs, lens.ctypes.data_as(C.c_void_p), C.byref(h))
+        else:
+            rc = lib().oracle_setup(C.c_int(self.n), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                                    v.ctypes.data_as(C.c_void_p), dp.ctypes.data_as(C.c_void_p),
+                                    ip.ctypes.data_as(C.c_void_p), C.byref(h))
         if rc != 0:
             raise ValueError(f"oracle_setup failed ({rc})")
         self._h = h

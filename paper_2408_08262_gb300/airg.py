@@ -60,6 +60,8 @@ def lib():
             raise ImportError(f"libairg.so not built ({LIB_PATH}); run paper_2408_08262_gb300.build.build()")
         L = C.CDLL(LIB_PATH)
         L.airg_setup.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_setup_reuse.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.c_int, C.c_void_p,
+                                       C.POINTER(C.c_void_p)]
         L.airg_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts), C.POINTER(_Info), C.c_void_p]
         L.airg_solve_host.argtypes = L.airg_solve.argtypes
         L.airg_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -90,7 +92,7 @@ def lib():
     return _lib
 
 
-EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_transpose", "airg_transpose", "airg_sddmm",
+EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_reuse", "airg_setup_transpose", "airg_transpose", "airg_sddmm",
             "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split", "airg_batch_create",
             "airg_solve_batched", "airg_batch_free",
             "airg_cf_split_noalloc",
@@ -151,16 +153,23 @@ def _csr(rowptr, col, val) -> _Csr:
 class Hierarchy:
     """An AIRG hierarchy built on the GPU (airg_setup)."""
 
-    def __init__(self, rowptr, col, val, params: Params | None = None, stream=None, transpose: bool = False):
-        """transpose=True builds the hierarchy of A^T (airg_setup_transpose), for adjoint solves."""
+    def __init__(self, rowptr, col, val, params: Params | None = None, stream=None, transpose: bool = False,
+                 reuse: "Hierarchy | None" = None, reuse_levels: int = 0):
+        """transpose=True builds the hierarchy of A^T (airg_setup_transpose), for adjoint solves.
+        reuse=T takes the CF splittings of T's first reuse_levels levels (0: all) instead of computing
+        them (airg_setup_reuse); the matrix should share T's sparsity pattern."""
         self.params = params or Params()
         self._keep = (rowptr, col, val)
         A = _csr(rowptr, col, val)
         self.n = A.n
         h = C.c_void_p()
-        fn = lib().airg_setup_transpose if transpose else lib().airg_setup
-        _check(fn(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)),
-               "airg_setup_transpose" if transpose else "airg_setup")
+        if reuse is not None:
+            _check(lib().airg_setup_reuse(C.byref(A), C.byref(self.params.c()), reuse._h, reuse_levels,
+                                          _stream(stream), C.byref(h)), "airg_setup_reuse")
+        else:
+            fn = lib().airg_setup_transpose if transpose else lib().airg_setup
+            _check(fn(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)),
+                   "airg_setup_transpose" if transpose else "airg_setup")
         self._h = h
 
     def close(self):

@@ -101,10 +101,15 @@ static int keep_polynomial(const LevelBuild& L, SolveLevel& S, Arena& a, cudaStr
   return AIRG_OK;
 }
 
-int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
+int setup_impl(airg_hierarchy* H, const airg_csr* Ain, const airg_hierarchy* T, int reuse_levels) {
   cudaStream_t s = H->s;
   SetupParams sp = to_setup(H->p);
   if (sp.coarse_size <= 0) sp.coarse_size = (int)std::min<long long>(60000, std::max<long long>(64, (long long)Ain->n / 16));
+  if (T) {  // setup re-use: the template's splittings for its leading non-coarsest levels
+    const int avail = (int)T->lv.size() - 1;
+    const int k = reuse_levels <= 0 ? avail : std::min(reuse_levels, avail);
+    for (int l = 0; l < k; ++l) sp.cf_reuse.push_back(T->lv[l].cf);
+  }
   Arena tmp;
   tmp.s = s;
   struct Rel {
@@ -203,6 +208,8 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain) {
     }
     S.nf = L.nf;
     S.nc = L.nc;
+    AIRG_TRY(H->solve_mem.alloc(&S.cf, std::max(L.n, 1)));
+    CU_TRY(cudaMemcpyAsync(S.cf, L.cf, (size_t)L.n, cudaMemcpyDeviceToDevice, s));
     const int* lay_next = (l + 1 < nl - 1) ? H->lv[l + 1].lay : nullptr;
     AIRG_TRY(build_solve_ops(L, lay_next, S.AF, S.Z, &S.w, S.W, H->solve_mem, tmp, s));
     if (S.W.nrows > 0) S.lanes_W = pick_lanes(avg_len(S.W));
@@ -357,12 +364,14 @@ void airg_params_default(airg_params* p) {
   p->ideal_prolong = 0;
 }
 
-int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
+static int setup_common(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out,
+                        const airg_hierarchy* T, int reuse_levels) {
   if (!out) return AIRG_ERR_ARG;
   *out = nullptr;
   AIRG_TRY(check_csr_arg(A));
   AIRG_TRY(check_params(p));
   if (A->n == 0) return AIRG_ERR_ARG;
+  if (T && T->n0 != A->n) return AIRG_ERR_ARG;
   airg_hierarchy* H = new (std::nothrow) airg_hierarchy;
   if (!H) return AIRG_ERR_OOM;
   H->p = *p;
@@ -384,7 +393,7 @@ int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, ai
     cudaGetLastError();
   }
   auto t0 = std::chrono::steady_clock::now();
-  int rc = setup_impl(H, A);
+  int rc = setup_impl(H, A, T, reuse_levels);
   if (rc != AIRG_OK) {
     cudaGetLastError();
     destroy(H);
@@ -393,6 +402,19 @@ int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, ai
   H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = H;
   return AIRG_OK;
+}
+
+int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
+  return setup_common(A, p, stream, out, nullptr, 0);
+}
+
+int airg_setup_reuse(const airg_csr* A, const airg_params* p, const airg_hierarchy* T, int levels,
+                     airg_stream_t stream, airg_hierarchy** out) {
+  if (!T) {
+    if (out) *out = nullptr;
+    return AIRG_ERR_ARG;
+  }
+  return setup_common(A, p, stream, out, T, levels);
 }
 
 int airg_solve(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* opts, airg_solve_info* info,

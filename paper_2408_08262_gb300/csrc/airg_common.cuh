@@ -202,7 +202,15 @@ struct SetupParams {
   uint64_t seed;
   int sparsity_order = 1;  // fixed sparsity of the A_ff polynomials: 1 pattern(A_ff), 2 pattern(A_ff^2)
   int ideal_prolong = 0;   // 1: P = [W; I] with W = -Ainv A_fc (drop_R), else one-point
+  // re-used CF splittings: cf_reuse[l] (device int8, level l's size) replaces the split of level l
+  // for l < n_reuse
+  std::vector<const int8_t*> cf_reuse;
 };
+
+// Level l's splitting taken from elsewhere (setup re-use): copies cf_in, computes the strength
+// flags the one-point prolongator needs, and counts the F-points (synchronises the stream).
+int reuse_split(const DCsr& A, const SetupParams& p, const int8_t* cf_in, int8_t* cf, uint8_t* strong, int* nf_out,
+                Arena& tmp, cudaStream_t s);
 
 // CF splitting of A (natural numbering); cf: device int8 n (1 F, 2 C).  strong (device uint8 nnz)
 // receives the strength flags when non-null.  nf_out: number of F-points.

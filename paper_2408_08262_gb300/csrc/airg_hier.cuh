@@ -17,6 +17,7 @@ struct SolveLevel {
   DCsr Z;     // restrictor rows in the next level's numbering (n_c x n_f)
   int* w = nullptr;  // one-point prolongation source per F-point (next level's numbering)
   int* lay = nullptr;  // natural index of this level -> nested solve position (non-coarsest)
+  int8_t* cf = nullptr;  // the level's CF splitting (non-coarsest), kept for setup re-use
   DCsr A;     // coarsest level only: the level matrix
   int lanes_AF = 4, lanes_Ainv = 4, lanes_Z = 4, lanes_A = 4;
   // mixed precision: the same operators with float or bf16 values (nullptr in FP64 mode)

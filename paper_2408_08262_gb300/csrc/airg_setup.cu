@@ -472,6 +472,25 @@ __global__ void k_isF(int n, const int8_t* __restrict__ cf, int* __restrict__ f)
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     f[i] = cf[i] == kF;
 }
+
+int reuse_split(const DCsr& A, const SetupParams& p, const int8_t* cf_in, int8_t* cf, uint8_t* strong, int* nf_out,
+                Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  CU_TRY(cudaMemcpyAsync(cf, cf_in, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  int *nS, *isF, *fpos;
+  AIRG_TRY(tmp.alloc(&nS, std::max(n, 1)));
+  AIRG_TRY(tmp.alloc(&isF, std::max(n, 1)));
+  AIRG_TRY(tmp.alloc(&fpos, (size_t)n + 1));
+  if (n > 0) {
+    airg::note_launch(), k_strength<<<GRID(n)>>>(n, A.rp, A.ci, A.v, p.strong_threshold, strong, nS);
+    airg::note_launch(), k_isF<<<GRID(n)>>>(n, cf, isF);
+  }
+  KERNEL_CHECK();
+  long long nf = 0;
+  AIRG_TRY(scan_i32(isF, fpos, n, tmp, s, &nf));  // synchronises
+  *nf_out = (int)nf;
+  return AIRG_OK;
+}
 // fpos: exclusive scan of isF.  pos(i) = F ? fpos(i) : nf + (i - fpos(i)).
 __global__ void k_cf_maps(int n, int nf, const int8_t* __restrict__ cf, const int* __restrict__ fpos, int* __restrict__ pos,
                           int* __restrict__ Fnat, int* __restrict__ Cnat) {
@@ -1173,14 +1192,18 @@ __global__ void __launch_bounds__(128) k_spgemm_thread(SpgArgs g, int* mid_rows,
         const double bv = g.bv[q];
         int pos = u;
         while (pos > 0 && cand[pos - 1] > j) --pos;
+        // integer work (search, insertion) may diverge; the one FMA per product sits after it, where
+        // the lanes meet again: an FP64 instruction costs sm_103a's FP64 pipe the same time with
+        // few lanes as with all, so one shared FMA instead of one per branch
         if (pos > 0 && cand[pos - 1] == j) {
-          acc[pos - 1] = fma(a, bv, acc[pos - 1]);
-          continue;
+          --pos;
+        } else {
+          for (int t = u; t > pos; --t) { cand[t] = cand[t - 1]; acc[t] = acc[t - 1]; }
+          cand[pos] = j;
+          acc[pos] = 0.0;
+          ++u;
         }
-        for (int t = u; t > pos; --t) { cand[t] = cand[t - 1]; acc[t] = acc[t - 1]; }
-        cand[pos] = j;
-        acc[pos] = fma(a, bv, 0.0);
-        ++u;
+        acc[pos] = fma(a, bv, acc[pos]);
       }
       }
     }
@@ -1834,7 +1857,10 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
     AIRG_TRY(own.alloc(&L.cf, n));
     AIRG_TRY(tmp.alloc(&strong, std::max(A.nnz, 1)));
     int nf = 0;
-    AIRG_TRY(cf_split(A, p, level, L.cf, strong, &nf, tmp, s));
+    if (level < (int)p.cf_reuse.size() && p.cf_reuse[level])
+      AIRG_TRY(reuse_split(A, p, p.cf_reuse[level], L.cf, strong, &nf, tmp, s));
+    else
+      AIRG_TRY(cf_split(A, p, level, L.cf, strong, &nf, tmp, s));
     if (nf == 0 || nf == n) coarsest = true;
     L.nf = nf;
     L.nc = n - nf;

@@ -403,5 +403,14 @@ def adjoint_2d(mesh_n: int = 256, theta: float = 1.1, config_index: int = 4) -> 
     return p1_dg_2d(mesh_n, theta, q=1.0, seed=derive_seed(config_index, 0), sigma_uniform=(0.0, 2.0))
 
 
+def groups_2d(mesh_n: int = 512, ngroups: int = 4, theta: float = 0.3, config_index: int = 5) -> list[Problem]:
+    """Energy groups of one mesh and direction: the blocked sigma pattern of blocked_sigma_2d with
+    its values {0, 1, 10} scaled by 0.1 * 4^g for group g; every group has the same sparsity
+    pattern (the setup re-use workload)."""
+    seed = derive_seed(config_index, 0)
+    return [p1_dg_2d(mesh_n, theta, q=1.0, seed=seed, sigma_blocks=(8, tuple(v * 0.1 * 4.0 ** g for v in (0.0, 1.0, 10.0))))
+            for g in range(ngroups)]
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(n)

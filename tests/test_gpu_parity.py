@@ -333,6 +333,47 @@ def test_ideal_prolongator_interpolates_the_exact_f_values_on_gpu():
     assert np.abs(x[F] - (xs[F] - b[F])).max() <= 1e-12 * sc
 
 
+def test_setup_reuse_matches_the_oracle_with_the_same_splittings():
+    # another energy group set up with the template group's splittings on every level
+    gs = P.groups_2d(64, ngroups=4)
+    op = O.Params()
+    T = airg.Hierarchy(*dev(gs[0]), gpu_params(op))
+    cf = [T.vectors(l)["cf"] for l in range(T.num_levels - 1)]
+    g = gs[3]
+    Hr = airg.Hierarchy(*dev(g), gpu_params(op), reuse=T)
+    assert Hr.num_levels == T.num_levels
+    Ho = O.Hierarchy(g.rowptr, g.col, g.val, op, cf=cf)
+    for l in range(Hr.num_levels - 1):
+        assert np.array_equal(Hr.vectors(l)["cf"], cf[l])
+    assert_csr_close(Ho.export(0, "Z"), Hr.export(0, "Z"), what="Z")
+    assert_csr_close(Ho.export(1, "A"), Hr.export(1, "A"), what="A_c")
+    xo, io = Ho.solve(g.b, rtol=1e-12, max_it=300)
+    xg, ig = Hr.solve(torch.from_numpy(g.b).cuda(), rtol=1e-12, max_it=300)
+    assert ig["status"] == 0 and io["status"] == 0
+    xg = xg.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    # a matrix of another size is refused
+    q = P.groups_2d(32, ngroups=1)[0]
+    with pytest.raises(airg.AirgError):
+        airg.Hierarchy(*dev(q), gpu_params(op), reuse=T)
+
+
+def test_setup_reuse_with_strength_zero_is_a_fresh_setup():
+    # strength 0: the level-0 splitting depends on the pattern only, so re-using it is exact
+    gs = P.groups_2d(64, ngroups=3)
+    par = airg.Params(strong_threshold=0.0)
+    T = airg.Hierarchy(*dev(gs[0]), par)
+    g = gs[2]
+    b = torch.from_numpy(g.b).cuda()
+    Hf = airg.Hierarchy(*dev(g), par)
+    Hr = airg.Hierarchy(*dev(g), par, reuse=T, reuse_levels=1)
+    xf, i_f = Hf.solve(b, rtol=1e-10)
+    xr, i_r = Hr.solve(b, rtol=1e-10)
+    assert i_f["status"] == 0 and i_f["iters"] == i_r["iters"]
+    assert torch.equal(xf, xr)
+
+
 def test_polynomial_order_trend():
     """Section "GMRES polynomial order" (table of orders 1-6): with first-order fixed sparsity the
     iteration count falls steeply from order 1 and flattens by order 4-6."""

@@ -604,6 +604,58 @@ def test_ideal_prolongator_solution_matches_dense_lu():
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
 
 
+def test_strength_zero_splitting_depends_on_the_pattern_only():
+    # Sections "Strong tolerances" and "Conclusions": with strength threshold 0 every connection is
+    # strong, PMISR picks an independent set of the matrix graph and A_ff is diagonal, so DDC
+    # (theta = 0 everywhere) converts nothing: the splitting is a function of the pattern alone and
+    # is the same for every energy group of a mesh and direction
+    gs = P.groups_2d(24, ngroups=3)
+    par = O.Params(strong_threshold=0.0)
+    cfs = [O.cf_split(g.rowptr, g.col, g.val, par) for g in gs]
+    for d in cfs:
+        assert np.array_equal(d["cf"], cfs[0]["cf"])
+        assert np.array_equal(d["cf"], d["cf_pmisr"])
+    # with the default strength 0.5 the splittings of the groups differ
+    c5 = [O.cf_split(g.rowptr, g.col, g.val, O.Params())["cf"] for g in gs]
+    assert not np.array_equal(c5[0], c5[2])
+
+
+def test_forced_splittings_reproduce_the_computed_hierarchy():
+    # the setup with every level's splitting given is the setup that computed them
+    p = P.groups_2d(24, ngroups=1)[0]
+    par = O.Params(coarse_size=32)
+    H = O.Hierarchy(p.rowptr, p.col, p.val, par)
+    L = H.num_levels
+    assert L > 3
+    cf = [H.vectors(l)["cf"] for l in range(L - 1)]
+    Hf = O.Hierarchy(p.rowptr, p.col, p.val, par, cf=cf)
+    assert Hf.num_levels == L
+    for l in range(L):
+        for which in ("A", "Ainv") + (("Z", "Aff") if l < L - 1 else ()):
+            for x, y in zip(H.export(l, which), Hf.export(l, which)):
+                assert np.array_equal(x, y), (l, which)
+    b = np.random.default_rng(0).standard_normal(p.n)
+    assert np.array_equal(H.vcycle(b), Hf.vcycle(b))
+    with pytest.raises(ValueError):
+        O.Hierarchy(p.rowptr, p.col, p.val, par, cf=[cf[0][:-1]])
+
+
+def test_reused_splittings_give_a_convergent_solver():
+    # another group's splittings on every level: a valid splitting (diagonals kept), so AIRG still
+    # solves to the dense LU solution
+    gs = P.groups_2d(16, ngroups=4)
+    par = O.Params(coarse_size=16)
+    T = O.Hierarchy(gs[0].rowptr, gs[0].col, gs[0].val, par)
+    cf = [T.vectors(l)["cf"] for l in range(T.num_levels - 1)]
+    g = gs[3]
+    H = O.Hierarchy(g.rowptr, g.col, g.val, par, cf=cf)
+    assert H.num_levels == T.num_levels
+    xs = O.dense_solve(g.rowptr, g.col, g.val, g.b)
+    x, info = H.solve(g.b, rtol=1e-12, max_it=300)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
+
+
 def test_matrix_free_airg_solution_matches_dense_lu():
     p = P.streaming_2d(16)
     xs = O.dense_solve(p.rowptr, p.col, p.val, p.b)
