@@ -417,6 +417,37 @@ def main():
                            "iters": [x[2] for x in r], "all_converged": all(x[3] == 0 for x in r)}
         reuse["setup_speedup"] = round(sum(x[0] for x in rows["fresh"]) / sum(x[0] for x in rows["reuse"]), 3)
 
+    # diagnostics of the splitting on every level of the 128x128 system: theta over the F-points
+    # after PMISR alone and after DDC (airg_ddc_theta on the GPU; histogram on [0, 1.5)), and the
+    # condition number of A_ff on levels small enough for a dense SVD on the host
+    diag = None
+    if not args.no_forms:
+        pd = P.blocked_sigma_2d(128)
+        Hd = airg.Hierarchy(*(torch.from_numpy(a).to(dev) for a in (pd.rowptr, pd.col, pd.val)),
+                            airg.Params(keep_setup=1))
+        diag = {"workload": "2D upwind P1 DG, 128x128 (98,304 DOFs), same generator as the main line",
+                "levels": []}
+        for l in range(Hd.num_levels - 1):
+            lrp, lci, lv = Hd.export(l, "A")
+            Ad = [torch.from_numpy(a).to(dev) for a in (lrp, lci, lv)]
+            cf_after = torch.from_numpy(Hd.vectors(l)["cf"]).to(dev)
+            cf_before = airg.cf_split(*Ad, airg.Params(ddc_fraction=0.0), level=l)
+            row = {"level": l, "n": int(lrp.size - 1)}
+            for tag, cf in (("pmisr", cf_before), ("pmisr_ddc", cf_after)):
+                th = airg.ddc_theta(*Ad, cf).cpu().numpy()
+                F = np.flatnonzero(cf.cpu().numpy() == 1)
+                h, _ = np.histogram(th[F], bins=10, range=(0.0, 1.5))
+                ent = {"n_f": int(F.size), "theta_max": round(float(th[F].max()), 4) if F.size else 0.0,
+                       "theta_hist_0_1.5": h.tolist()}
+                if 0 < F.size <= 4000:
+                    M = np.zeros((lrp.size - 1, lrp.size - 1))
+                    M[np.repeat(np.arange(lrp.size - 1), np.diff(lrp)), lci] = lv
+                    sv = np.linalg.svd(M[np.ix_(F, F)], compute_uv=False)
+                    ent["cond_aff"] = round(float(sv[0] / sv[-1]), 3)
+                row[tag] = ent
+            diag["levels"].append(row)
+        Hd.close()
+
     # batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle graph,
     # against the same 64 systems solved one after another (same hierarchies)
     batched, adjoint = None, None
@@ -512,7 +543,7 @@ def main():
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "mixed_precision_forms": forms,
                 "batched_form": batched, "adjoint_form": adjoint, "poly_order_sweep": poly_sweep,
-                "setup_reuse_form": reuse,
+                "setup_reuse_form": reuse, "splitting_diagnostics": diag,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

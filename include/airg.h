@@ -212,6 +212,14 @@ int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf
 int airg_cf_split_noalloc(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out,
                           airg_stream_t stream);
 
+/* Diagnostic (the diagonal-dominance ratios behind DDC, Algorithm 2 and Section "CF splitting"):
+ * theta_i = sum_{j in F, j != i} |a_ij| / |a_ii| over the F-points of the splitting cf (device, n
+ * int8, 1 = F, 2 = C), 0 for C-points and for F rows with no F neighbour.  theta: device, n FP64.
+ * Sums run over the row in storage order.  The splitting before DDC is the one airg_cf_split gives
+ * with ddc_fraction = 0.  Synchronises the stream.  Errors: AIRG_ERR_ARG, AIRG_ERR_CSR,
+ * AIRG_ERR_ZERO_DIAG, AIRG_ERR_CUDA. */
+int airg_ddc_theta(const airg_csr* A, const int8_t* cf, double* theta, airg_stream_t stream);
+
 /* Frees a hierarchy and everything it owns (NULL is allowed).  Synchronises the stream the
  * hierarchy was built on. */
 void airg_free(airg_hierarchy* H);

@@ -66,6 +66,7 @@ def lib():
         L.airg_solve_host.argtypes = L.airg_solve.argtypes
         L.airg_vcycle.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.airg_cf_split.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
+        L.airg_ddc_theta.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p]
         L.airg_cf_split_noalloc.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_int, C.c_void_p, C.c_void_p]
         L.airg_setup_transpose.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
         L.airg_transpose.argtypes = [C.POINTER(_Csr), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -92,7 +93,7 @@ def lib():
     return _lib
 
 
-EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_reuse", "airg_setup_transpose", "airg_transpose", "airg_sddmm",
+EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_reuse", "airg_setup_transpose", "airg_ddc_theta", "airg_transpose", "airg_sddmm",
             "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split", "airg_batch_create",
             "airg_solve_batched", "airg_batch_free",
             "airg_cf_split_noalloc",
@@ -310,6 +311,19 @@ def cf_split(rowptr, col, val, params: Params | None = None, level: int = 0, str
     _check(lib().airg_cf_split(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf.data_ptr()), _stream(stream)),
            "airg_cf_split")
     return cf
+
+
+def ddc_theta(rowptr, col, val, cf, stream=None):
+    """airg_ddc_theta: theta_i = sum_{j in F, j != i} |a_ij| / |a_ii| for the F-points of the
+    splitting cf (CUDA int8, 1 = F, 2 = C); a CUDA float64 tensor, 0 on C-points."""
+    import torch
+    A = _csr(rowptr, col, val)
+    if not (cf.is_cuda and cf.dtype == torch.int8 and cf.numel() == A.n):
+        raise TypeError("cf must be a CUDA int8 tensor with one entry per row")
+    theta = torch.empty(A.n, dtype=torch.float64, device=rowptr.device)
+    _check(lib().airg_ddc_theta(C.byref(A), C.c_void_p(cf.data_ptr()), C.c_void_p(theta.data_ptr()),
+                                _stream(stream)), "airg_ddc_theta")
+    return theta
 
 
 def cf_split_noalloc(rowptr, col, val, cf_out, params: Params | None = None, level: int = 0, stream=None):

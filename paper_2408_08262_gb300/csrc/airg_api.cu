@@ -491,6 +491,26 @@ int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf
   return rc;
 }
 
+int airg_ddc_theta(const airg_csr* A, const int8_t* cf, double* theta, airg_stream_t stream) {
+  AIRG_TRY(check_csr_arg(A));
+  if (!cf || !theta) return AIRG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena tmp;
+  tmp.s = s;
+  DCsr D;
+  D.nrows = D.ncols = A->n;
+  D.nnz = A->nnz;
+  D.rp = const_cast<int*>(A->rowptr);
+  D.ci = const_cast<int*>(A->col);
+  D.v = const_cast<double*>(A->val);
+  int rc = validate_csr(D, tmp, s);
+  if (rc == AIRG_OK) rc = ddc_theta(D, cf, theta, tmp, s);
+  if (rc == AIRG_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  tmp.release();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
 void airg_free(airg_hierarchy* H) { destroy(H); }
 
 int airg_num_levels(const airg_hierarchy* H) { return H ? (int)H->lv.size() : AIRG_ERR_ARG; }

@@ -207,6 +207,10 @@ struct SetupParams {
   std::vector<const int8_t*> cf_reuse;
 };
 
+// theta_i = sum_{j in F, j != i} |a_ij| / |a_ii| for the F-points of cf (0 for C-points), the
+// quantity DDC ranks (Algorithm 2).
+int ddc_theta(const DCsr& A, const int8_t* cf, double* theta, Arena& tmp, cudaStream_t s);
+
 // Level l's splitting taken from elsewhere (setup re-use): copies cf_in, computes the strength
 // flags the one-point prolongator needs, and counts the F-points (synchronises the stream).
 int reuse_split(const DCsr& A, const SetupParams& p, const int8_t* cf_in, int8_t* cf, uint8_t* strong, int* nf_out,

@@ -278,6 +278,16 @@ __global__ void k_ddc_theta(int n, const int* __restrict__ rp, const int* __rest
   if (nc) atomicAdd(counts + 1, nc);
 }
 
+int ddc_theta(const DCsr& A, const int8_t* cf, double* theta, Arena& tmp, cudaStream_t s) {
+  const int n = A.nrows;
+  int* ctr;
+  AIRG_TRY(tmp.alloc(&ctr, 4));
+  CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * 4, s));
+  if (n > 0) airg::note_launch(), k_ddc_theta<<<GRID(n)>>>(n, A.rp, A.ci, A.v, cf, theta, ctr);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
 struct RadixState {
   unsigned long long prefix, mask;
   long long krem;

@@ -70,6 +70,24 @@ def test_cf_split_bitexact_top_level(mesh, theta, alpha, loops):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("mesh", [64, 33])
+def test_ddc_theta_matches_oracle_bitexact(mesh):
+    # airg_ddc_theta on the PMISR splitting (DDC fraction 0) is the oracle's theta bit for bit; on
+    # the final splitting every F-point is below the oracle's threshold tau
+    p = P.p1_dg_2d(mesh, 0.3, seed=mesh + 11, sigma_uniform=(0.0, 2.0))
+    d = O.cf_split(p.rowptr, p.col, p.val, O.Params())
+    rp, ci, v = dev(p)
+    cf0 = airg.cf_split(rp, ci, v, airg.Params(ddc_fraction=0.0))
+    assert np.array_equal(cf0.cpu().numpy(), d["cf_pmisr"])
+    th0 = airg.ddc_theta(rp, ci, v, cf0).cpu().numpy()
+    assert np.array_equal(th0, d["theta"])
+    cf1 = airg.cf_split(rp, ci, v, airg.Params())
+    th1 = airg.ddc_theta(rp, ci, v, cf1).cpu().numpy()
+    F = cf1.cpu().numpy() == 1
+    assert np.all(th1[F] < d["tau"]) and np.all(th1[~F] == 0)
+    assert th0[d["cf_pmisr"] == 1].max() > th1[F].max()
+
+
 def test_cf_split_bitexact_3d():
     p = P.kuhn_3d(10)
     op = O.Params()

@@ -208,6 +208,25 @@ def test_ddc_threshold_property():
     assert np.all(th2[after == 1] <= th[after == 1])
 
 
+@pytest.mark.parametrize("mk", [lambda: P.streaming_2d(16), lambda: P.blocked_sigma_2d(16), lambda: P.streaming_2d(24)])
+def test_ddc_diagnostics_theta_and_aff_condition(mk):
+    # Section "CF splitting" reports that DDC brings the largest theta over the F-points from about
+    # 1 down to about 0.6 (PMISR alone leaves rows with F-F coupling as large as the diagonal), and
+    # Table cond_aff relates that to the conditioning of A_ff: both, on the top level
+    p = mk()
+    A = p.scipy().toarray()
+    d = O.cf_split(p.rowptr, p.col, p.val, O.Params())
+    th_max, kappa = [], []
+    for cf in (d["cf_pmisr"], d["cf"]):
+        _, th, _ = O.ddc(p.rowptr, p.col, p.val, cf, 0.0)
+        F = np.flatnonzero(cf == 1)
+        th_max.append(th[F].max())
+        s = np.linalg.svd(A[np.ix_(F, F)], compute_uv=False)
+        kappa.append(s[0] / s[-1])
+    assert th_max[0] > 0.9 and th_max[1] < 0.7
+    assert kappa[1] <= kappa[0] * (1 + 1e-12)
+
+
 def test_zero_strength_gives_diagonal_aff_and_ddc_noop():
     # Section "Strong tolerances": strength 0.0 gives an independent set in the adjacency graph,
     # a diagonal A_ff, and DDC ignores diagonal rows.
