@@ -886,11 +886,9 @@ int poly_fit(const DCsr& A, int m, uint64_t seed, int level, double* alpha, int*
   KERNEL_CHECK();
   const int lanes = pick_lanes((double)A.nnz / std::max(1, n));
   for (int c = 1; c < nc; ++c) AIRG_TRY(dev_spmv(A, K + (size_t)(c - 1) * n, nullptr, K + (size_t)c * n, SPMV_SET, lanes, s));
-  int* dfit;
-  AIRG_TRY(tmp.alloc(&dfit, 1));
-  AIRG_TRY(tsqr_fit(K, n, nc, m, alpha, dfit, tmp, s));
-  CU_TRY(cudaMemcpyAsync(fitted, dfit, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CU_TRY(cudaStreamSynchronize(s));
+  // the fitted count stays on the device (read back once the hierarchy is built): no host
+  // synchronisation here, so the work queued after the fit (the side stream's P and A P) overlaps it
+  AIRG_TRY(tsqr_fit(K, n, nc, m, alpha, fitted, tmp, s));
   return AIRG_OK;
 }
 
