@@ -481,7 +481,24 @@ def main():
                    "iters_min": min(i["iters"] for i in infos), "iters_max": max(i["iters"] for i in infos),
                    "all_converged": all(i["status"] == 0 for i in infos),
                    "iters_sequential_max": max(its_seq)}
+        # the SpMV autotuner's choices, and the batched solve with the row-length rule alone
+        tuned = Bt.tuned()
         Bt.close()
+        os.environ["AIRG_NO_AUTOTUNE"] = "1"
+        try:
+            Br = airg.Batch(Hs)
+        finally:
+            del os.environ["AIRG_NO_AUTOTUNE"]
+        Br.solve(bs, rtol=args.rtol)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        Br.solve(bs, rtol=args.rtol)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        Br.close()
+        batched["autotuner"] = {"groups_tuned": len(tuned), "changed_from_rule": sum(r != c for r, c in tuned),
+                                "rule_vs_chosen_lanes": tuned,
+                                "batched_solve_ms_rule_lanes": round(e0.elapsed_time(e1), 2)}
         del Hs
         # adjoint form: J = w . u on 256 x 256 (393,216 DOFs) with per-element sigma; forward solve
         # and backward (A^T hierarchy + adjoint solve + SDDMM) through the autograd Function

@@ -186,6 +186,15 @@ int airg_solve_batched(airg_batch* B, const double* const* b, double* const* x, 
                        airg_solve_info* infos, airg_stream_t stream);
 void airg_batch_free(airg_batch* B);
 
+/* The batched form's SpMV autotuner.  airg_batch_create times every lanes-per-row variant (1, 2, 4,
+ * ..., 32 lanes per row) of each grouped operator with at least 16384 rows and keeps the fastest;
+ * smaller groups keep the row-length rule.  Setting the environment variable AIRG_NO_AUTOTUNE=1
+ * keeps the rule everywhere.  The variants sum a row in different orders, so the chosen variants
+ * can change results in the last bits.  airg_batch_tuned writes, for the first `cap` tuned groups,
+ * the rule's lanes and the chosen lanes (host arrays; either may be NULL) and returns the number of
+ * tuned groups. */
+int airg_batch_tuned(const airg_batch* B, int* rule_lanes, int* chosen_lanes, int cap);
+
 /* One V-cycle from a zero guess, x = M b (b, x: device, n).  For tests and diagnostics. */
 int airg_vcycle(airg_hierarchy* H, const double* b, double* x, airg_stream_t stream);
 

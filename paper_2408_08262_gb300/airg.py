@@ -74,6 +74,7 @@ def lib():
         L.airg_batch_create.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
         L.airg_solve_batched.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts), C.c_void_p, C.c_void_p]
         L.airg_batch_free.argtypes = [C.c_void_p]
+        L.airg_batch_tuned.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.airg_batch_free.restype = None
         L.airg_free.argtypes = [C.c_void_p]
         L.airg_free.restype = None
@@ -95,7 +96,7 @@ def lib():
 
 EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_reuse", "airg_setup_transpose", "airg_ddc_theta", "airg_transpose", "airg_sddmm",
             "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split", "airg_batch_create",
-            "airg_solve_batched", "airg_batch_free",
+            "airg_solve_batched", "airg_batch_free", "airg_batch_tuned",
             "airg_cf_split_noalloc",
             "airg_free", "airg_num_levels", "airg_level_info", "airg_export_csr", "airg_export_vectors", "airg_export_layout",
             "airg_profile_enable", "airg_kernel_times", "airg_kernel_times_level", "airg_launch_count",
@@ -349,6 +350,14 @@ class Batch:
         b = C.c_void_p()
         _check(lib().airg_batch_create(arr, len(self.H), _stream(stream), C.byref(b)), "airg_batch_create")
         self._b = b
+
+    def tuned(self) -> list:
+        """(rule lanes, chosen lanes) of every group the SpMV autotuner timed (airg_batch_tuned)."""
+        n = lib().airg_batch_tuned(self._b, None, None, 0)
+        rule = (C.c_int * max(n, 1))()
+        chosen = (C.c_int * max(n, 1))()
+        lib().airg_batch_tuned(self._b, rule, chosen, n)
+        return [(rule[k], chosen[k]) for k in range(n)]
 
     def close(self):
         if getattr(self, "_b", None):

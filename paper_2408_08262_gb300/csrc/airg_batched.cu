@@ -260,9 +260,61 @@ struct airg_batch {
   cudaGraphExec_t vg = nullptr;
   cudaStream_t cap = nullptr;
   long long vg_kernels = 0;
+  // SpMV autotuner: lanes per row of every grouped operator picked by timing (AIRG_NO_AUTOTUNE=1:
+  // the row-length rule alone); scratch vectors for the trial launches
+  bool tune = true;
+  double *tx = nullptr, *ty = nullptr;
+  std::vector<std::pair<int, int>> tuned;  // (rule's lanes, chosen lanes) per tuned group
 };
 
 namespace {
+
+// The autotuner: every lanes-per-row variant of the grouped SpMV (1, 2, 4, ..., 32) runs on the
+// group's operator (SET into scratch vectors, one untimed launch then kTuneReps timed with CUDA
+// events on the batch's stream), and the fastest is kept.  Groups below kTuneMinRows rows keep the
+// row-length rule: their launches are latency-bound whatever the variant.  The row sums of
+// different variants round differently, so a batch's results can change in the last bits with the
+// variants chosen.
+constexpr long long kTuneMinRows = 16384;
+constexpr int kTuneReps = 3;
+
+int tune_lanes(airg_batch* B, Group& g) {
+  cudaStream_t s = B->s;
+  if (!B->tx) {
+    AIRG_TRY(B->mem.alloc(&B->tx, (size_t)std::max(B->N, 1LL)));
+    AIRG_TRY(B->mem.alloc(&B->ty, (size_t)std::max(B->N, 1LL)));
+    CU_TRY(cudaMemsetAsync(B->tx, 0, sizeof(double) * (size_t)std::max(B->N, 1LL), s));
+  }
+  cudaEvent_t e0, e1;
+  CU_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return AIRG_ERR_CUDA;
+  }
+  const int rule = g.lanes;
+  int best = rule;
+  float best_ms = 0.f;
+  int rc = AIRG_OK;
+  for (int lanes = 1; lanes <= 32 && rc == AIRG_OK; lanes *= 2) {
+    g.lanes = lanes;
+    rc = spmv_mapped(g, B->tx, nullptr, B->ty, SPMV_SET, s);
+    if (rc == AIRG_OK) rc = cuda_status(cudaEventRecord(e0, s));
+    for (int r = 0; r < kTuneReps && rc == AIRG_OK; ++r) rc = spmv_mapped(g, B->tx, nullptr, B->ty, SPMV_SET, s);
+    if (rc == AIRG_OK) rc = cuda_status(cudaEventRecord(e1, s));
+    if (rc == AIRG_OK) rc = cuda_status(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    if (rc == AIRG_OK) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+    if (rc == AIRG_OK && (lanes == 1 || ms < best_ms)) {
+      best_ms = ms;
+      best = lanes;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.lanes = best;
+  B->tuned.push_back({rule, best});
+  return rc;
+}
 
 int concat_group(airg_batch* B, std::vector<std::pair<int, const DCsr*>>& parts, std::vector<int>& col_off,
                  std::vector<int>& map_off, Group& g) {
@@ -291,6 +343,7 @@ int concat_group(airg_batch* B, std::vector<std::pair<int, const DCsr*>>& parts,
   CU_TRY(cudaStreamSynchronize(s));  // `last` lives on the host stack
   g.lanes = pick_lanes((double)nnz / (double)rows);
   KERNEL_CHECK();
+  if (B->tune && rows >= kTuneMinRows) AIRG_TRY(tune_lanes(B, g));
   return AIRG_OK;
 }
 
@@ -492,6 +545,10 @@ int airg_batch_create(airg_hierarchy* const* Hs, int nsys, airg_stream_t stream,
   }
   airg_batch* B = new (std::nothrow) airg_batch;
   if (!B) return AIRG_ERR_OOM;
+  {
+    const char* t = getenv("AIRG_NO_AUTOTUNE");
+    B->tune = !(t && t[0] == '1');
+  }
   B->nsys = nsys;
   B->s = (cudaStream_t)stream;
   B->mem.s = B->s;
@@ -514,6 +571,16 @@ void airg_batch_free(airg_batch* B) {
   cudaStreamSynchronize(B->s);
   if (B->hsc) cudaFreeHost(B->hsc);
   delete B;
+}
+
+int airg_batch_tuned(const airg_batch* B, int* rule_lanes, int* chosen_lanes, int cap) {
+  if (!B || cap < 0) return AIRG_ERR_ARG;
+  const int n = (int)B->tuned.size();
+  for (int k = 0; k < n && k < cap; ++k) {
+    if (rule_lanes) rule_lanes[k] = B->tuned[k].first;
+    if (chosen_lanes) chosen_lanes[k] = B->tuned[k].second;
+  }
+  return n;
 }
 
 int airg_solve_batched(airg_batch* B, const double* const* b, double* const* x, const airg_solve_opts* o,

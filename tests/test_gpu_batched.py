@@ -58,3 +58,25 @@ def test_batched_restarts_and_per_system_status():
     zero = [torch.zeros_like(b) for b in bs]
     xs, infos = B.solve(zero, rtol=1e-10)
     assert all(i["iters"] == 0 for i in infos) and all(torch.count_nonzero(x) == 0 for x in xs)
+
+
+def test_batched_autotuner_picks_lanes_and_keeps_the_solution(monkeypatch):
+    # the autotuner times every lanes-per-row variant of the large grouped operators; the chosen
+    # variants change only the rounding of the row sums
+    ps = systems()
+    par = airg.Params(coarse_size=64)
+    Hs = [airg.Hierarchy(*dev(p), par) for p in ps]
+    bs = [torch.from_numpy(p.b).cuda() for p in ps]
+    B = airg.Batch(Hs)
+    tuned = B.tuned()
+    assert tuned and all(r in (1, 2, 4, 8, 16, 32) and c in (1, 2, 4, 8, 16, 32) for r, c in tuned)
+    xs, infos = B.solve(bs, rtol=1e-12)
+    B.close()
+    monkeypatch.setenv("AIRG_NO_AUTOTUNE", "1")
+    Br = airg.Batch(Hs)
+    assert Br.tuned() == []
+    xr, ir = Br.solve(bs, rtol=1e-12)
+    Br.close()
+    for x, i, y, j in zip(xs, infos, xr, ir):
+        assert i["status"] == 0 and j["status"] == 0 and abs(i["iters"] - j["iters"]) <= 1
+        assert (torch.linalg.norm(x - y) / torch.linalg.norm(y)).item() <= 1e-10
