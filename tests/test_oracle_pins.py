@@ -72,6 +72,21 @@ def test_generator_matrix_structure():
     assert np.all(q.scipy().diagonal() > 0)
 
 
+def test_energy_groups_share_the_pattern():
+    # the setup re-use workload: groups of one mesh and direction differ in values only, and the
+    # removal term only adds to each element's own block (the sigma-free part is the same)
+    gs = P.groups_2d(8, ngroups=3)
+    for g in gs[1:]:
+        assert np.array_equal(g.rowptr, gs[0].rowptr) and np.array_equal(g.col, gs[0].col)
+        assert not np.array_equal(g.val, gs[0].val)
+    d = [g.scipy() - gs[0].scipy() for g in gs[1:]]
+    elem = np.arange(gs[0].n) // 3
+    for D in d:
+        D = D.tocoo()
+        nz = D.data != 0
+        assert nz.any() and np.all(elem[D.row[nz]] == elem[D.col[nz]])
+
+
 # ---------------------------------------------------------------------------------------------
 # Strength of connection (eq. soc)
 # ---------------------------------------------------------------------------------------------
