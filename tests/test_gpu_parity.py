@@ -472,11 +472,13 @@ def test_setup_is_deterministic_run_to_run():
     assert i1 == i2 and torch.equal(x1, x2)
 
 
-@pytest.mark.parametrize("variant", [{}, {"matrix_free": 1}, {"ideal_prolong": 1}])
-def test_sliced_ell_and_csr_solves_agree_bitwise(monkeypatch, variant):
+@pytest.mark.parametrize("mesh,variant", [(160, {}), (160, {"matrix_free": 1}), (160, {"ideal_prolong": 1}),
+                                          (150, {})])
+def test_sliced_ell_and_csr_solves_agree_bitwise(monkeypatch, mesh, variant):
     # the sliced ELL SpMV keeps each row's CSR entry order and accumulates from zero with one FMA
-    # per entry, as the CSR row kernel does: the solves are bitwise identical
-    p = P.blocked_sigma_2d(160)  # 153,600 rows: the top levels take the sliced form
+    # per entry, as the CSR row kernel does: the solves are bitwise identical.  160^2 gives 153,600
+    # rows (150 full 1024-row windows); 150^2 gives 135,000 (a ragged last window and slice)
+    p = P.blocked_sigma_2d(mesh)
     b = torch.from_numpy(p.b).cuda()
     Hs = airg.Hierarchy(*dev(p), airg.Params(**variant))
     assert Hs.level_info(-1)["top_sell"] == 1
