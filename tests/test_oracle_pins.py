@@ -306,6 +306,30 @@ def test_poly_degree1_normal_equations():
     np.testing.assert_allclose(alpha, ref, rtol=1e-10)
 
 
+@pytest.mark.parametrize("m", [3, 5, 7])
+def test_poly_minimises_the_residual_like_lstsq(m):
+    # eq. gmres_poly: the coefficients minimise ||b - A q(A) b|| over polynomials q of degree m-1,
+    # a least-squares problem on [A b, ..., A^m b] that numpy solves by SVD (not by the oracle's
+    # Householder TSQR and Givens solve)
+    rng = np.random.default_rng(40 + m)
+    n = 60
+    M = sp.random(n, n, density=0.1, random_state=50 + m) * 0.5 + sp.diags(1.0 + rng.random(n))
+    rp, ci, v = to_csr(M.toarray())
+    b = rng.standard_normal(n)
+    alpha, mf = O.poly_fit(rp, ci, v, m, b)
+    assert mf == m
+    K = np.empty((n, m))
+    w = b.copy()
+    for k in range(m):
+        w = M @ w
+        K[:, k] = w
+    ref = np.linalg.lstsq(K, b, rcond=None)[0]
+    res, res_ref = np.linalg.norm(b - K @ alpha), np.linalg.norm(b - K @ ref)
+    assert res <= res_ref * (1 + 1e-10) + 1e-14
+    assert res < 0.9 * np.linalg.norm(b)
+    np.testing.assert_allclose(alpha, ref, rtol=1e-6, atol=1e-8 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("n", [2, 3, 5, 6])
 def test_poly_degree_n_minus_1_is_exact_inverse(n):
     # Cayley-Hamilton: for a dense n x n matrix (fixed sparsity = full pattern, closed under
