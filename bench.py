@@ -33,7 +33,7 @@ UNIT = "DOFs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="airg", choices=["airg", "reference"])
     ap.add_argument("--mesh", type=int, default=1024)
