@@ -61,6 +61,16 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, dist, device) -> float:
+    """The sum of a per-rank float over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_value(dofs_per_rank: int, steps: int, world: int, seconds: float) -> float:
     """Whole-job throughput: the DOFs every rank solved in `steps` steps, over the slowest rank's time."""
     return dofs_per_rank * steps * world / seconds
@@ -195,6 +205,76 @@ def reference_arm(args, rank):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batched_form(args, airg, P, torch, dev, stream, params, dist, world: int, rank: int) -> dict:
+    """The batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle
+    graph, against the same systems solved one after another (same hierarchies).  Under torchrun
+    the systems are partitioned over the ranks by nonzero count (no data exchange: each rank solves
+    its share) and the times are the slowest rank's."""
+    from paper_2408_08262_gb300 import shard
+    systems_all = P.batched_2d(64)
+    mine = shard.partition([len(q.col) for q in systems_all], world)[rank]
+    systems = [systems_all[i] for i in mine]
+    infos, its_seq, tuned = [], [], []
+    tb = ts = tr = 0.0
+    if systems:
+        Hs, bs = [], []
+        for q in systems:
+            Hs.append(airg.Hierarchy(*(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)), params))
+            bs.append(torch.from_numpy(q.b).to(dev))
+        Bt = airg.Batch(Hs)
+        Bt.solve(bs, rtol=args.rtol)
+        for H, bq in zip(Hs, bs):
+            H.solve(bq, rtol=args.rtol)
+        torch.cuda.synchronize(dev)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        xs, infos = Bt.solve(bs, rtol=args.rtol)
+        e1.record(stream)
+        for H, bq in zip(Hs, bs):
+            _, ii = H.solve(bq, rtol=args.rtol)
+            its_seq.append(ii["iters"])
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        # the SpMV autotuner's choices, and the batched solve with the row-length rule alone
+        tuned = Bt.tuned()
+        Bt.close()
+        os.environ["AIRG_NO_AUTOTUNE"] = "1"
+        try:
+            Br = airg.Batch(Hs)
+        finally:
+            del os.environ["AIRG_NO_AUTOTUNE"]
+        Br.solve(bs, rtol=args.rtol)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        Br.solve(bs, rtol=args.rtol)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tr = e0.elapsed_time(e1)
+        Br.close()
+        del Hs
+    tb = max_over_ranks(tb, dist, dev)
+    ts = max_over_ranks(ts, dist, dev)
+    tr = max_over_ranks(tr, dist, dev)
+    ndofs = int(sum_over_ranks(sum(q.n for q in systems), dist, dev))
+    nsys = int(sum_over_ranks(len(systems), dist, dev))
+    it_min = -max_over_ranks(-min((i["iters"] for i in infos), default=10 ** 9), dist, dev)
+    it_max = max_over_ranks(max((i["iters"] for i in infos), default=0), dist, dev)
+    it_seq = max_over_ranks(max(its_seq, default=0), dist, dev)
+    failed = max_over_ranks(float(any(i["status"] != 0 for i in infos)), dist, dev)
+    batched = {"workload": "64 P1 DG systems, n x n with n drawn from {64,128,256,512}, theta ~ U[0,2pi), "
+                           "sigma ~ U[0,5]", "systems": nsys, "total_dofs": ndofs, "ranks": world,
+               "systems_per_rank_max": int(max_over_ranks(len(systems), dist, dev)),
+               "batched_solve_ms": round(tb, 2), "sequential_solve_ms": round(ts, 2),
+               "speedup_vs_sequential": round(ts / tb, 3), "batched_dofs_per_s": ndofs / (tb / 1e3),
+               "iters_min": int(it_min), "iters_max": int(it_max), "all_converged": failed == 0.0,
+               "iters_sequential_max": int(it_seq)}
+    batched["autotuner"] = {"groups_tuned": len(tuned), "changed_from_rule": sum(r != c for r, c in tuned),
+                            "rule_vs_chosen_lanes": tuned, "batched_solve_ms_rule_lanes": round(tr, 2),
+                            "note": "choices of rank 0" if world > 1 else "one rank"}
+    return batched
 
 
 def main():
@@ -448,58 +528,10 @@ def main():
             diag["levels"].append(row)
         Hd.close()
 
-    # batched form: 64 independent systems of uneven size, grouped kernels and one V-cycle graph,
-    # against the same 64 systems solved one after another (same hierarchies)
+    # batched form (see batched_form); the adjoint form follows
     batched, adjoint = None, None
     if not args.no_forms:
-        systems = P.batched_2d(64)
-        Hs, bs = [], []
-        for q in systems:
-            Hs.append(airg.Hierarchy(*(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)), params))
-            bs.append(torch.from_numpy(q.b).to(dev))
-        Bt = airg.Batch(Hs)
-        Bt.solve(bs, rtol=args.rtol)
-        for H, bq in zip(Hs, bs):
-            H.solve(bq, rtol=args.rtol)
-        torch.cuda.synchronize(dev)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        xs, infos = Bt.solve(bs, rtol=args.rtol)
-        e1.record(stream)
-        its_seq = []
-        for H, bq in zip(Hs, bs):
-            _, ii = H.solve(bq, rtol=args.rtol)
-            its_seq.append(ii["iters"])
-        e2.record(stream)
-        torch.cuda.synchronize(dev)
-        tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
-        ndofs = sum(q.n for q in systems)
-        batched = {"workload": "64 P1 DG systems, n x n with n drawn from {64,128,256,512}, theta ~ U[0,2pi), "
-                               "sigma ~ U[0,5]", "systems": len(systems), "total_dofs": ndofs,
-                   "batched_solve_ms": round(tb, 2), "sequential_solve_ms": round(ts, 2),
-                   "speedup_vs_sequential": round(ts / tb, 3), "batched_dofs_per_s": ndofs / (tb / 1e3),
-                   "iters_min": min(i["iters"] for i in infos), "iters_max": max(i["iters"] for i in infos),
-                   "all_converged": all(i["status"] == 0 for i in infos),
-                   "iters_sequential_max": max(its_seq)}
-        # the SpMV autotuner's choices, and the batched solve with the row-length rule alone
-        tuned = Bt.tuned()
-        Bt.close()
-        os.environ["AIRG_NO_AUTOTUNE"] = "1"
-        try:
-            Br = airg.Batch(Hs)
-        finally:
-            del os.environ["AIRG_NO_AUTOTUNE"]
-        Br.solve(bs, rtol=args.rtol)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        Br.solve(bs, rtol=args.rtol)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        Br.close()
-        batched["autotuner"] = {"groups_tuned": len(tuned), "changed_from_rule": sum(r != c for r, c in tuned),
-                                "rule_vs_chosen_lanes": tuned,
-                                "batched_solve_ms_rule_lanes": round(e0.elapsed_time(e1), 2)}
-        del Hs
+        batched = batched_form(args, airg, P, torch, dev, stream, params, dist, world, rank)
         # adjoint form: J = w . u on 256 x 256 (393,216 DOFs) with per-element sigma; forward solve
         # and backward (A^T hierarchy + adjoint solve + SDDMM) through the autograd Function
         qa = P.adjoint_2d(256)
