@@ -27,6 +27,20 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as C99 with no torch or C++ types
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "airg.h"\nint main(void) { airg_params p; airg_params_default(&p); return p.seed == 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                        "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(libpath):
     lib = ctypes.CDLL(libpath)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
