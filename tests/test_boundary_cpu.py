@@ -72,3 +72,28 @@ def test_setup_rejects_null_arguments_without_gpu(libpath):
     out = ctypes.c_void_p()
     assert airg.lib().airg_setup(None, None, None, ctypes.byref(out)) == -1
     assert airg.lib().airg_solve(None, None, None, None, None, None) == -1
+
+
+def test_parameter_and_argument_checks_run_before_any_device_work(libpath):
+    # the variants' parameter rules and the new entry points' argument checks are host-side: they
+    # reject before the library touches the device (the CSR pointers below are never dereferenced)
+    from paper_2408_08262_gb300 import airg
+    L = airg.lib()
+    A = airg._Csr(8, 8, 16, 32, 48)  # n, nnz, non-null stand-in pointers
+    out = ctypes.c_void_p()
+
+    def setup(**kw):
+        p = airg.Params(**kw).c()
+        return L.airg_setup(ctypes.byref(A), ctypes.byref(p), None, ctypes.byref(out))
+
+    for bad in (dict(matrix_free=2), dict(matrix_free=1, precision=1), dict(matrix_free=1, precision=2),
+                dict(ideal_prolong=3), dict(ideal_prolong=1, precision=1), dict(sparsity_order=3),
+                dict(sparsity_order=0), dict(poly_order=15), dict(coarse_iters=0), dict(strong_threshold=1.5),
+                dict(ddc_fraction=-0.1), dict(precision=7)):
+        assert setup(**bad) == -1, bad
+        assert out.value is None
+    p = airg.Params().c()
+    assert L.airg_setup_reuse(ctypes.byref(A), ctypes.byref(p), None, 0, None, ctypes.byref(out)) == -1
+    assert L.airg_ddc_theta(None, None, None, None) == -1
+    assert L.airg_ddc_theta(ctypes.byref(A), None, None, None) == -1
+    assert L.airg_batch_tuned(None, None, None, 0) == -1
