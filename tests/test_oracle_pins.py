@@ -478,6 +478,28 @@ def test_coarse_matrix_is_RAP():
     assert np.all((dropped < 0.01 * rowmax) | (dropped == 0))
 
 
+def test_one_point_prolongation_hand_worked_fixture():
+    # Setup step 10 (classical one-point operator, Section "Results"): the choice of every F-row of
+    # a hand-worked 10-point example with a given splitting, covering a tie (smaller index, by
+    # magnitude), the fallback to weak C entries, a transpose-only strong dependency (not used),
+    # a stored zero (never chosen) and a strong F neighbour larger than every C entry.
+    g = gold("one_point_example.json")
+    rp, ci, v = (np.array(g[k], dtype=t) for k, t in (("rowptr", np.int32), ("col", np.int32), ("val", np.float64)))
+    cf = np.array(g["cf"], dtype=np.int8)
+    F = np.flatnonzero(cf == 1)
+    Cn = np.flatnonzero(cf == 2)
+    # the strength flags the choice is made from
+    st = O.cf_split(rp, ci, v, O.Params(strong_threshold=g["alpha"]))["strong"]
+    for f, i in enumerate(F):
+        assert st[rp[i]:rp[i + 1]].tolist() == g["strong_F_rows"][f], i
+    par = O.Params(strong_threshold=g["alpha"], max_levels=2, coarse_size=1, poly_order=2, coarse_poly_order=3)
+    H = O.Hierarchy(rp, ci, v, par, cf=[cf])
+    vec = H.vectors(0)
+    assert np.array_equal(vec["cf"], cf)
+    expect = [-1 if j < 0 else int(np.flatnonzero(Cn == j)[0]) for j in g["w_natural"]]
+    assert vec["w"].tolist() == expect
+
+
 def test_one_point_prolongation_picks_strongest_C():
     p = P.streaming_2d(8)
     H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params(max_levels=2))
