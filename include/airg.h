@@ -208,16 +208,20 @@ int airg_cf_split(const airg_csr* A, const airg_params* p, int level, int8_t* cf
  * allocating routine) at the point they need the splitting -- for example a program that reserves
  * all device memory at start-up and allocates nothing afterwards, or a latency-critical loop in
  * which an allocation, and the synchronisation it may trigger, is not acceptable.
- * All temporaries live in one fixed 32 MiB device array that the library reserves on every GPU it
- * is loaded on and keeps until the process exits.  The input needs about 5 bytes per nonzero plus
- * 34 bytes per row; larger inputs return AIRG_ERR_SCRATCH before any GPU work.  The result is
- * identical to airg_cf_split's (same kernels, same arithmetic).
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- *     that first call outside any stream capture.
+ * All temporaries live in one fixed 32 MiB device array.  The input needs about 5 bytes per
+ * nonzero plus 34 bytes per row; larger inputs return AIRG_ERR_SCRATCH before any GPU work.  The
+ * result is identical to airg_cf_split's (same kernels, same arithmetic), and so are the argument
+ * checks (AIRG_ERR_ARG) and the cf_out encoding.
+ *   - The first call on a device is the set-up: CUDA loads the library's modules lazily, so that
+ *     call loads the kernels the splitting launches and the array itself (allocated then, and held
+ *     until the process exits), and looks up the array's device address (cudaGetSymbolAddress).
+ *     It allocates device memory: make it at start-up, before reserving the rest of the device,
+ *     and outside any stream capture.  Later calls allocate nothing.  After a device reset
+ *     (cudaDeviceReset) the next call on that device is a first call again.
  *   - Every call shares the one array.  Calls that can overlap on the GPU (other streams, other
  *     host threads) race on it and must be serialised by the caller.  Each call clears what it
  *     needs; the array otherwise keeps the last call's contents.
- *   - Synchronises the stream.  Same arguments and cf_out encoding as airg_cf_split. */
+ *   - Synchronises the stream. */
 int airg_cf_split_noalloc(const airg_csr* A, const airg_params* p, int level, int8_t* cf_out,
                           airg_stream_t stream);
 

@@ -332,8 +332,10 @@ def cf_split_noalloc(rowptr, col, val, cf_out, params: Params | None = None, lev
     with no device allocation inside the library (for callers that cannot allocate at that point;
     see include/airg.h for the capacity and the sharing rules)."""
     A = _csr(rowptr, col, val)
-    if not (cf_out.is_cuda and cf_out.numel() == A.n):
-        raise TypeError("cf_out must be a CUDA int8 tensor with one entry per row")
+    import torch
+    if not (cf_out.is_cuda and cf_out.dtype == torch.int8 and cf_out.is_contiguous() and cf_out.numel() == A.n
+            and cf_out.device == rowptr.device):
+        raise TypeError("cf_out must be a contiguous int8 CUDA tensor on the matrix's device, one entry per row")
     p = params or Params()
     _check(lib().airg_cf_split_noalloc(C.byref(A), C.byref(p.c()), level, C.c_void_p(cf_out.data_ptr()),
                                        _stream(stream)), "airg_cf_split_noalloc")

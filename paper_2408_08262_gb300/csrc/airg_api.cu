@@ -37,22 +37,6 @@ SetupParams to_setup(const airg_params& p) {
   return q;
 }
 
-int check_params(const airg_params* p) {
-  if (!p) return AIRG_ERR_ARG;
-  if (!(p->strong_threshold >= 0.0 && p->strong_threshold <= 1.0)) return AIRG_ERR_ARG;
-  if (!(p->ddc_fraction >= 0.0 && p->ddc_fraction <= 1.0)) return AIRG_ERR_ARG;
-  if (p->poly_order < 0 || p->poly_order > 14 || p->coarse_poly_order < 0 || p->coarse_poly_order > 14) return AIRG_ERR_ARG;
-  if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0) return AIRG_ERR_ARG;
-  if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
-  if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
-  if (p->sparsity_order != 1 && p->sparsity_order != 2) return AIRG_ERR_ARG;
-  if (p->matrix_free != 0 && p->matrix_free != 1) return AIRG_ERR_ARG;
-  if (p->matrix_free && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
-  if (p->ideal_prolong != 0 && p->ideal_prolong != 1) return AIRG_ERR_ARG;
-  if (p->ideal_prolong && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
-  return AIRG_OK;
-}
-
 // Algorithmic bytes of one SpMV with the given epilogue: the CSR arrays once, x once per column
 // (every solve operator references essentially all of its columns), y written once, and b
 // (RESID/ADDB) or y (ADD) read once.
@@ -333,13 +317,34 @@ void destroy(airg_hierarchy* H) {
   delete H;
 }
 
+}  // namespace
+
+namespace airg {
+
+// Host-side argument checks shared by the entry points (nothing is read on the device).
+int check_params(const airg_params* p) {
+  if (!p) return AIRG_ERR_ARG;
+  if (!(p->strong_threshold >= 0.0 && p->strong_threshold <= 1.0)) return AIRG_ERR_ARG;
+  if (!(p->ddc_fraction >= 0.0 && p->ddc_fraction <= 1.0)) return AIRG_ERR_ARG;
+  if (p->poly_order < 0 || p->poly_order > 14 || p->coarse_poly_order < 0 || p->coarse_poly_order > 14) return AIRG_ERR_ARG;
+  if (p->coarse_iters < 1 || p->max_levels < 1 || p->n_smooth_up < 0) return AIRG_ERR_ARG;
+  if (!(p->drop_R >= 0.0) || !(p->drop_Ac >= 0.0)) return AIRG_ERR_ARG;
+  if (p->precision != AIRG_FP64 && p->precision != AIRG_FP32 && p->precision != AIRG_BF16_VALUES) return AIRG_ERR_ARG;
+  if (p->sparsity_order != 1 && p->sparsity_order != 2) return AIRG_ERR_ARG;
+  if (p->matrix_free != 0 && p->matrix_free != 1) return AIRG_ERR_ARG;
+  if (p->matrix_free && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
+  if (p->ideal_prolong != 0 && p->ideal_prolong != 1) return AIRG_ERR_ARG;
+  if (p->ideal_prolong && p->precision != AIRG_FP64) return AIRG_ERR_ARG;
+  return AIRG_OK;
+}
+
 int check_csr_arg(const airg_csr* A) {
   if (!A || A->n < 0 || A->nnz < 0) return AIRG_ERR_ARG;
   if (A->n > 0 && (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val)))) return AIRG_ERR_ARG;
   return AIRG_OK;
 }
 
-}  // namespace
+}  // namespace airg
 
 extern "C" {
 

@@ -296,4 +296,9 @@ int permute_matrix(const DCsr& A, const int* pos, DCsr& out, Arena& own, Arena& 
 // Input validation: sorted unique in-range columns, nonzero diagonal.
 int validate_csr(const DCsr& A, Arena& tmp, cudaStream_t s);
 
+// Host-side argument checks of the entry points (airg_api.cu): null pointers, negative sizes and
+// parameters outside their ranges give AIRG_ERR_ARG before any device work.
+int check_params(const airg_params* p);
+int check_csr_arg(const airg_csr* A);
+
 }  // namespace airg

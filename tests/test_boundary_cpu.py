@@ -97,3 +97,21 @@ def test_parameter_and_argument_checks_run_before_any_device_work(libpath):
     assert L.airg_ddc_theta(None, None, None, None) == -1
     assert L.airg_ddc_theta(ctypes.byref(A), None, None, None) == -1
     assert L.airg_batch_tuned(None, None, None, 0) == -1
+    # the entry point without allocation takes airg_cf_split's argument checks, before its capacity
+    # check and before any device work
+    cfo = ctypes.c_void_p(64)
+    for bad in (dict(poly_order=15), dict(coarse_iters=0), dict(strong_threshold=1.5), dict(precision=7),
+                dict(matrix_free=2), dict(sparsity_order=3)):
+        p = airg.Params(**bad).c()
+        assert L.airg_cf_split_noalloc(ctypes.byref(A), ctypes.byref(p), 0, cfo, None) == -1, bad
+        assert L.airg_cf_split(ctypes.byref(A), ctypes.byref(p), 0, cfo, None) == -1, bad
+    p = airg.Params().c()
+    assert L.airg_cf_split_noalloc(None, ctypes.byref(p), 0, cfo, None) == -1
+    assert L.airg_cf_split_noalloc(ctypes.byref(A), None, 0, cfo, None) == -1
+    assert L.airg_cf_split_noalloc(ctypes.byref(A), ctypes.byref(p), 0, None, None) == -1
+    assert L.airg_cf_split_noalloc(ctypes.byref(A), ctypes.byref(p), -1, cfo, None) == -1
+    Anull = airg._Csr(8, 8, None, 32, 48)
+    assert L.airg_cf_split_noalloc(ctypes.byref(Anull), ctypes.byref(p), 0, cfo, None) == -1
+    # beyond the fixed array: rejected with its own code, still before any device work
+    Abig = airg._Csr(10_000_000, 100_000_000, 16, 32, 48)
+    assert L.airg_cf_split_noalloc(ctypes.byref(Abig), ctypes.byref(p), 0, cfo, None) == -8

@@ -25,6 +25,28 @@ def dev(p):
     return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (p.rowptr, p.col, p.val))
 
 
+def test_noalloc_first_and_then_without_any_device_allocation():
+    # In a fresh process this is the library's first call on the device: it loads the kernels and
+    # the array (CUDA loads modules on first use), so only the calls after it are checked for
+    # allocations.  Free device memory and torch's reserved pool must not move across them, and
+    # every result must equal the allocating entry point's, computed afterwards.
+    p = P.blocked_sigma_2d(96)
+    rp, ci, v = dev(p)
+    params = airg.Params()
+    outs = [torch.full((p.n,), -1, dtype=torch.int8, device="cuda") for _ in range(3)]
+    airg.cf_split_noalloc(rp, ci, v, outs[0], params)
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for out in outs[1:]:
+        airg.cf_split_noalloc(rp, ci, v, out, params)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_reserved() == reserved0
+    ref = airg.cf_split(rp, ci, v, params)
+    for out in outs:
+        assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("mesh,level", [(64, 0), (128, 3)])
 def test_noalloc_matches_the_allocating_entry_point_on_two_calls(mesh, level):
     p = P.blocked_sigma_2d(mesh)
