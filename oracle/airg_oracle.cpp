@@ -1,4 +1,4 @@
-// AIRG oracle: plain, slow, single-thread FP64 CPU restatement of the reduction multigrid of
+// AIRG oracle: plain, slow, FP64 CPU restatement of the reduction multigrid of
 // Dargaville, Smedley-Stevenson, Smith & Pain, "Coarsening and parallelism with reduction
 // multigrids for hyperbolic Boltzmann transport" (arXiv 2408.08262).
 //
@@ -21,7 +21,9 @@
 //
 // Where arithmetic order can change the last bit, this code fixes the order to the plain
 // definition: sums run in ascending index order; products accumulated by std::fma.  Compiled with
-// -ffp-contract=off so the compiler adds no fusion of its own.
+// -ffp-contract=off so the compiler adds no fusion of its own.  Everything runs on one thread
+// except, on request (oracle_set_threads), the rows of the SpMV, which are independent: any
+// thread count gives bitwise the same results.
 
 #include <algorithm>
 #include <cmath>
@@ -54,9 +56,15 @@ Csr make_csr(int nr, int nc, const int* rp, const int* ci, const double* v) {
   return A;
 }
 
+// Threads of the SpMV row loop (1 unless oracle_set_threads asks for more; only the all-cores CPU
+// baseline does).  Rows are independent and each keeps its own summation order, so any thread
+// count gives bitwise the same result.
+int g_threads = 1;
+
 // y = A x, each row summed in ascending column order.
 void spmv(const Csr& A, const std::vector<double>& x, std::vector<double>& y) {
   y.assign(A.nrows, 0.0);
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
   for (int i = 0; i < A.nrows; ++i) {
     double s = 0.0;
     for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) s += A.v[k] * x[A.ci[k]];
@@ -970,6 +978,13 @@ void copy_csr(const Csr& A, int* rp, int* ci, double* v) {
 // Return codes: 0 ok, -1 bad argument / CSR, -2 singular, 1 not converged, -4 NaN.
 // =============================================================================================
 extern "C" {
+
+// Threads of the SpMV row loop (at least 1); returns the previous count.
+int oracle_set_threads(int t) {
+  const int prev = g_threads;
+  g_threads = t < 1 ? 1 : t;
+  return prev;
+}
 
 int oracle_setup(int n, const int* rp, const int* ci, const double* v, const double* dp, const long long* ip,
                  void** out) {

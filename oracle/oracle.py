@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so (plain g++, -O2, no FP contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
@@ -45,6 +45,8 @@ def lib():
         _lib.oracle_setup_forced.restype = C.c_int
         _lib.oracle_num_levels.restype = C.c_int
         _lib.oracle_free.restype = None
+        _lib.oracle_set_threads.restype = C.c_int
+        _lib.oracle_set_threads.argtypes = [C.c_int]
     return _lib
 
 
@@ -185,6 +187,12 @@ class Hierarchy:
         out = np.zeros(3)
         lib().oracle_complexities(self._h, out.ctypes.data_as(C.c_void_p))
         return dict(grid=out[0], operator=out[1], storage=out[2])
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's SpMV row loop (1 by default); returns the previous count.  Results are
+    bitwise the same for any count: rows are independent and keep their summation order."""
+    return int(lib().oracle_set_threads(int(t)))
 
 
 def cf_split(rowptr, col, val, params: Params | None = None, level: int = 0) -> dict:

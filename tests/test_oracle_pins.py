@@ -802,3 +802,21 @@ def test_zero_rhs_and_degenerate_sizes():
     assert Hd.num_levels == 1
     x, info = Hd.solve(np.ones(n), rtol=1e-12)
     np.testing.assert_allclose(x, 1 / np.linspace(1, 2, n), rtol=1e-10)
+
+
+def test_oracle_spmv_threads_give_bitwise_the_same_solve():
+    # the all-cores CPU baseline runs the oracle's SpMV row loop on several threads: rows are
+    # independent and keep their summation order, so hierarchy and solution must not change a bit
+    p = P.blocked_sigma_2d(48)
+    out = []
+    for t in (1, 3):
+        prev = O.set_threads(t)
+        try:
+            H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params())
+            x, info = H.solve(p.b, rtol=1e-10)
+            out.append((x, info["iters"], H.export(1, "A")))
+        finally:
+            O.set_threads(prev)
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a, b)
