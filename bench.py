@@ -182,6 +182,34 @@ def run_oracle_sample(mesh: int, rtol: float):
     return p.n, dt, info
 
 
+def cpu_baselines(args, p) -> dict:
+    """The oracle timed on the host cores on the benchmarked system itself: once on one thread, once
+    with its SpMV row loop on every core this process may run on (setup otherwise serial; results
+    bitwise those of one thread).  Setup and solve are timed separately."""
+    from oracle import oracle as O
+    O.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    runs = {}
+    for t in (1, cores):
+        O.set_threads(t)
+        t0 = time.perf_counter()
+        H = O.Hierarchy(p.rowptr, p.col, p.val, O.Params())
+        t1 = time.perf_counter()
+        x, info = H.solve(p.b, rtol=args.rtol)
+        t2 = time.perf_counter()
+        del H
+        runs[t] = (t1 - t0, t2 - t1, info)
+    O.set_threads(1)
+    su, so, info = runs[cores]
+    s1, o1, info1 = runs[1]
+    return {"value": p.n / (su + so), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one oracle setup + solve to rtol {args.rtol:g} of the benchmarked {args.mesh}x{args.mesh} "
+                      f"system ({p.n:,} DOFs); SpMV row loops on {cores} threads, the rest of setup serial: "
+                      f"setup {su:.1f} s, solve {so:.2f} s, {info['iters']} iterations",
+            "single_thread": {"value": p.n / (s1 + o1), "unit": UNIT, "cores": 1, "setup_s": round(s1, 2),
+                              "solve_s": round(o1, 2), "iters": info1["iters"]}}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -275,6 +303,59 @@ def batched_form(args, airg, P, torch, dev, stream, params, dist, world: int, ra
                             "rule_vs_chosen_lanes": tuned, "batched_solve_ms_rule_lanes": round(tr, 2),
                             "note": "choices of rank 0" if world > 1 else "one rank"}
     return batched
+
+
+def mixed_forms_3d(args, airg, P, torch, dev, stream, mesh: int = 128) -> dict:
+    """The mixed-precision form on its own configuration: 3D upwind P0 DG on mesh^3 cubes of six
+    Kuhn tetrahedra (12,582,912 DOFs at 128), FP64 against the FP32 and bf16-value V-cycles, each
+    set up and solved to rtol 1e-8 (time-to-rtol = setup + solve), with the per-class SpMV rates
+    of one profiled solve and the error against the FP64 GPU solution."""
+    import numpy as np
+    p3 = P.kuhn_3d(mesh)
+    rp3, ci3, v3, b3 = (torch.from_numpy(a).to(dev) for a in (p3.rowptr, p3.col, p3.val, p3.b))
+    out = {"workload": f"3D upwind P0 DG, {mesh}^3 cubes x 6 jittered Kuhn tets ({p3.n:,} DOFs, {p3.nnz:,} nnz), "
+                       "Omega=(0.48,0.60,0.64), sigma in {0,0.01} by a seeded half-space; setup + FGMRES(30) "
+                       "to rtol 1e-8"}
+    x64 = None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16_values", 2)):
+        par = airg.Params(precision=prec)
+        Hw = airg.Hierarchy(rp3, ci3, v3, par)
+        Hw.solve(b3, rtol=args.rtol, restart=args.restart)
+        Hw.close()
+        su, so, its = [], [], []
+        for _ in range(2):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            Hf = airg.Hierarchy(rp3, ci3, v3, par)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            xf, inf = Hf.solve(b3, rtol=args.rtol, restart=args.restart)
+            t2 = time.perf_counter()
+            su.append(1e3 * (t1 - t0))
+            so.append(1e3 * (t2 - t1))
+            its.append(inf["iters"])
+            if _ == 0:
+                lvi = Hf.level_info(-1)
+                Hf.profile()
+                Hf.solve(b3, rtol=args.rtol, restart=args.restart)
+                kt = Hf.kernel_times()
+            Hf.close()
+        ent = {"setup_ms": round(min(su), 2), "solve_ms": round(min(so), 2),
+               "time_to_rtol_ms": round(min(su) + min(so), 2), "iters": max(its), "relres": inf["relres"],
+               "levels": lvi["levels"], "operator_complexity": round(lvi["operator"], 3),
+               "dofs_per_s": p3.n / ((min(su) + min(so)) / 1e3),
+               "solve_spmv_GBps": {c: round(kt[c]["bytes"] / max(kt[c]["ms"], 1e-9) / 1e6, 1)
+                                   for c in ("smooth_resid", "smooth_update", "restrict", "top_op", "coarsest")}}
+        xh = xf.double()
+        if prec == 0:
+            x64 = xh
+        else:
+            ent["rel_err_vs_fp64_gpu"] = float(torch.linalg.norm(xh - x64) / torch.linalg.norm(x64))
+            ent["solve_speedup_vs_fp64"] = round(out["fp64"]["solve_ms"] / ent["solve_ms"], 3)
+            ent["time_to_rtol_speedup_vs_fp64"] = round(out["fp64"]["time_to_rtol_ms"] / ent["time_to_rtol_ms"], 3)
+        out[name] = ent
+    del rp3, ci3, v3, b3
+    return out
 
 
 def main():
@@ -528,6 +609,11 @@ def main():
             diag["levels"].append(row)
         Hd.close()
 
+    # the mixed-precision form on its own configuration (3D P0, 128^3)
+    forms3d = None
+    if not args.no_forms:
+        forms3d = mixed_forms_3d(args, airg, P, torch, dev, stream)
+
     # batched form (see batched_form); the adjoint form follows
     batched, adjoint = None, None
     if not args.no_forms:
@@ -567,12 +653,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import oracle as O
-        O.build()
-        n_s, dt_s, _ = run_oracle_sample(args.cpu_sample_mesh, args.rtol)
-        cpu = {"value": n_s / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one oracle setup+solve of the same generator at {args.cpu_sample_mesh}x"
-                         f"{args.cpu_sample_mesh} ({n_s:,} DOFs), single thread, {dt_s:.1f} s"}
+        cpu = cpu_baselines(args, p)
 
     if rank == 0:
         med = lambda a: sorted(a)[len(a) // 2]
@@ -591,6 +672,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (CSR alone %.0f MB)" % ((p.nnz * 12 + p.n * 4) / 1e6)},
                 "roofline": roofline, "cpu_baseline": cpu, "mixed_precision_forms": forms,
+                "mixed_precision_forms_3d": forms3d,
                 "batched_form": batched, "adjoint_form": adjoint, "poly_order_sweep": poly_sweep,
                 "setup_reuse_form": reuse, "splitting_diagnostics": diag,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
