@@ -285,9 +285,11 @@ int airg_export_layout(const airg_hierarchy* H, int level, int32_t* pos, int32_t
  * 0 disables, -1 times every class).  Every launch of a selected class is bracketed by CUDA events
  * on its stream; airg_kernel_times() returns, per kernel
  * class (0: smoother residual A_F*, 1: smoother update Ainv, 2: restriction Z, 3: top-level
- * operator, 4: coarsest level, 5: prolongation gather, 6: Gram-Schmidt passes), the launch count,
- * the summed milliseconds and the summed algorithmic bytes (CSR arrays + vectors read/written
- * once).  Every call of airg_profile_enable resets the sums. */
+ * operator, 4: coarsest level, 5: prolongation gather, 6: Gram-Schmidt passes, 7: whole V-cycle
+ * applications, each timed by one event pair outside the cycle, with the summed algorithmic bytes
+ * of all of the cycle's SpMVs), the launch count, the summed milliseconds and the summed
+ * algorithmic bytes (CSR arrays + vectors read/written once).  Every call of airg_profile_enable
+ * resets the sums. */
 int airg_profile_enable(airg_hierarchy* H, int enable);
 int airg_kernel_times(airg_hierarchy* H, int64_t* launches, double* ms, double* bytes, int nclasses);
 /* The same sums restricted to the launches that worked on hierarchy level `level` (classes 3 and 6

@@ -20,7 +20,8 @@ AIRG_OK, AIRG_NOT_CONVERGED = 0, 1
 STATUS = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "invalid CSR", -3: "zero diagonal",
           -4: "NaN", -5: "out of memory", -6: "CUDA error", -7: "unsupported",
           -8: "input larger than the no-allocation scratch array"}
-PROFILE_CLASSES = ["smooth_resid", "smooth_update", "restrict", "top_op", "coarsest", "prolong", "gram_schmidt"]
+PROFILE_CLASSES = ["smooth_resid", "smooth_update", "restrict", "top_op", "coarsest", "prolong", "gram_schmidt",
+                   "vcycle"]
 
 
 class AirgError(RuntimeError):
@@ -406,21 +407,59 @@ def sddmm(rowptr, col, lam, x, scale: float = 1.0, stream=None):
     return out
 
 
-def _solve_fn():
+class HierarchyCache:
+    """Hierarchies of the adjoint form kept for re-use: one for A (forward solves) and one for A^T
+    (backward solves), each for the most recent matrix.  A matrix is the same one when it is given by
+    the same three tensors (storage, offset, size, device) and none of them has been written since
+    (torch's version counter of each tensor); anything else builds a new hierarchy.  Only a
+    bookkeeping layer: the hierarchies and solves are the library's."""
+
+    def __init__(self):
+        self.entries = {}
+
+    @staticmethod
+    def key(rowptr, col, val, params, transpose):
+        def tk(t):
+            return (t.data_ptr(), t.numel(), t.dtype, str(t.device), t._version)
+        return (tk(rowptr), tk(col), tk(val), tuple(sorted(vars(params).items())), bool(transpose))
+
+    def get(self, rowptr, col, val, params, transpose=False):
+        k = self.key(rowptr, col, val, params, transpose)
+        ent = self.entries.get(transpose)
+        if ent is not None and ent[0] == k:
+            return ent[1]
+        if ent is not None:
+            ent[1].close()
+        H = Hierarchy(rowptr, col, val, params, transpose=transpose)
+        self.entries[transpose] = (k, H, (rowptr, col, val))  # the tensors stay alive with the entry
+        return H
+
+    def clear(self):
+        for ent in self.entries.values():
+            ent[1].close()
+        self.entries.clear()
+
+
+def _solve_fn(cache: "HierarchyCache | None"):
     import torch
 
     class SolveFn(torch.autograd.Function):
         """x = A^-1 b with AIRG-preconditioned FGMRES; differentiable in A's values and b.
 
         backward: lambda = A^-T g by an AIRG solve with the hierarchy of A^T (airg_setup_transpose);
-        dL/db = lambda and dL/dA = -lambda x^T on A's pattern (airg_sddmm)."""
+        dL/db = lambda and dL/dA = -lambda x^T on A's pattern (airg_sddmm).  With a cache, the
+        hierarchies of A and A^T are kept and re-used while the matrix tensors are unchanged."""
 
         @staticmethod
         def forward(ctx, rowptr, col, val, b, params=None, rtol=1e-12):
             par = params or Params()
-            H = Hierarchy(rowptr, col, val, par)
+            if cache is not None:
+                H = cache.get(rowptr, col, val, par)
+            else:
+                H = Hierarchy(rowptr, col, val, par)
             x, info = H.solve(b.contiguous(), rtol=rtol, max_it=500)
-            H.close()
+            if cache is None:
+                H.close()
             if info["status"] != 0:
                 raise AirgError(info["status"], "SolveFn forward")
             ctx.save_for_backward(rowptr, col, val, x)
@@ -430,9 +469,13 @@ def _solve_fn():
         @staticmethod
         def backward(ctx, gx):
             rowptr, col, val, x = ctx.saved_tensors
-            HT = Hierarchy(rowptr, col, val, ctx.params, transpose=True)
+            if cache is not None:
+                HT = cache.get(rowptr, col, val, ctx.params, transpose=True)
+            else:
+                HT = Hierarchy(rowptr, col, val, ctx.params, transpose=True)
             lam, info = HT.solve(gx.contiguous(), rtol=ctx.rtol, max_it=500)
-            HT.close()
+            if cache is None:
+                HT.close()
             if info["status"] != 0:
                 raise AirgError(info["status"], "SolveFn backward")
             gval = sddmm(rowptr, col, lam, x, -1.0) if ctx.needs_input_grad[2] else None
@@ -445,11 +488,15 @@ def _solve_fn():
 _SolveFn = None
 
 
-def solve_fn():
-    """The torch.autograd.Function of the adjoint form (SolveFn.apply(rowptr, col, val, b, params, rtol))."""
+def solve_fn(cache: "HierarchyCache | None" = None):
+    """The torch.autograd.Function of the adjoint form (SolveFn.apply(rowptr, col, val, b, params, rtol)).
+    With a HierarchyCache, forward and backward re-use the hierarchies of A and A^T while the matrix
+    tensors are unchanged (several right-hand sides, or an optimisation over the source only)."""
     global _SolveFn
+    if cache is not None:
+        return _solve_fn(cache)
     if _SolveFn is None:
-        _SolveFn = _solve_fn()
+        _SolveFn = _solve_fn(None)
     return _SolveFn
 
 

@@ -227,9 +227,15 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain, const airg_hierarchy* T, 
       return AIRG_OK;
     };
     AIRG_TRY(mk(H->A0s));
-    if (H->p.precision == AIRG_FP64)
-      for (auto& S : H->lv)
-        if (!S.coarsest) AIRG_TRY(mk(S.AF));
+    // [A_ff A_fc] in every precision: the mixed-precision V-cycle reads the copy's values cast to
+    // float or bf16
+    const int vt_sell = H->p.precision == AIRG_FP32 ? 1 : (H->p.precision == AIRG_BF16_VALUES ? 2 : 0);
+    for (auto& S : H->lv)
+      if (!S.coarsest) {
+        const size_t before = H->sells.size();
+        AIRG_TRY(mk(S.AF));
+        if (vt_sell && H->sells.size() > before) AIRG_TRY(sell_cast_values(H->sells.back(), vt_sell, H->solve_mem, s));
+      }
   }
   if (ev_layout1) cudaEventRecord(ev_layout1, s);
   // mixed-precision form: low-precision copies of every V-cycle operator
@@ -647,6 +653,7 @@ int airg_profile_enable(airg_hierarchy* H, int enable) {
       }
     }
     H->bytes_A0 = spmv_bytes(H->A0s, false);
+    H->bytes_V = vcycle_bytes(H);
   }
   H->prof.on = enable != 0;
   H->prof.mask = (unsigned)enable;

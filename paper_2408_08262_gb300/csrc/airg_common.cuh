@@ -45,6 +45,8 @@ struct DSell {
   int* ci = nullptr;
   double* v = nullptr;
   int* perm = nullptr;
+  void* v_lo = nullptr;  // the values as float (vt 1) or bf16 (vt 2) for the mixed-precision V-cycle
+  int vt = 0;
 };
 constexpr int kSellWindow = 1024;
 
@@ -168,6 +170,11 @@ bool want_sell(const DCsr& A);
 int build_sell(const DCsr& A, DSell& out, Arena& own, Arena& tmp, cudaStream_t s);
 int sell_spmv(const DSell& S, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
               const double* coef, cudaStream_t s);
+// Mixed precision: the copy's values cast to float (vt 1) or bf16 (vt 2); the SpMV with float
+// vectors and accumulation (the same modes, w != nullptr: RESID with the fused prolongation).
+int sell_cast_values(DSell& S, int vt, Arena& own, cudaStream_t s);
+int sell_spmv_lo(const DSell& S, const float* x, const float* b, float* y, int mode, const int* w, float* xf,
+                 cudaStream_t s);
 // y = coef[0] r, or y += coef[0] r with add (coef on the device); x += y
 void dev_coef_axpy(const double* coef, const double* r, double* y, int n, bool add, cudaStream_t s);
 void dev_add(const double* y, double* x, int n, cudaStream_t s);

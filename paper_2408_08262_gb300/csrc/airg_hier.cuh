@@ -36,7 +36,10 @@ struct SolveLevel {
   double bytes_mf = 0;  // algorithmic bytes of one matrix-free application
 };
 
-enum ProfClass { PC_SMOOTH_RESID = 0, PC_SMOOTH_UPDATE, PC_RESTRICT, PC_TOP_OP, PC_COARSEST, PC_PROLONG, PC_GS, PC_N };
+// Kernel classes timed by the profiler.  PC_VCYCLE times each whole V-cycle application (the graph
+// replay, or the eager sequence) with one event pair outside it, so it adds nothing inside the
+// cycle; its bytes are the sum of the algorithmic bytes of every SpMV of the cycle.
+enum ProfClass { PC_SMOOTH_RESID = 0, PC_SMOOTH_UPDATE, PC_RESTRICT, PC_TOP_OP, PC_COARSEST, PC_PROLONG, PC_GS, PC_VCYCLE, PC_N };
 
 struct Profiler {
   bool on = false;
@@ -80,6 +83,7 @@ struct airg_hierarchy {
   int* pos0 = nullptr;  // natural -> solve numbering (nullptr: identity)
   int lanes_A0 = 4;
   double bytes_A0 = 0;
+  double bytes_V = 0;  // algorithmic bytes of every SpMV of one V-cycle (vcycle_bytes)
   // workspaces (allocated on first solve)
   int restart_alloc = 0;
   double *V = nullptr, *Zk = nullptr, *w = nullptr, *r = nullptr, *bwork = nullptr, *rtmp = nullptr,
@@ -114,4 +118,6 @@ int prof_graph_read(airg_hierarchy* H);
 int solve_fgmres(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
 int solve_richardson(airg_hierarchy* H, const double* b, double* x, const airg_solve_opts* o, airg_solve_info* info);
 int prof_flush(airg_hierarchy* H);
+// Algorithmic bytes of one V-cycle: the sum of the byte counts its SpMV classes are timed with.
+double vcycle_bytes(const airg_hierarchy* H);
 }  // namespace airg

@@ -384,7 +384,7 @@ __device__ __forceinline__ XT row_entries(const int* __restrict__ ci, const VT* 
 // the lines they touch arrive once in L1), up to the warp's longest row, and accumulates with one
 // fused multiply-add per entry, in storage order; no shared memory and no barrier.
 template <typename VT, typename XT, int MODE, bool PROLONG, int kRowBatch>
-__global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(256, (kRowBatch == 4 && !PROLONG) ? 8 : 1) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
                                                   const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
   for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < nrows; rr += (long long)gridDim.x * blockDim.x) {
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256) k_spmv_row(int nrows, const int* __restri
 // lane l taking entries l, l + LPR, ... (4 per batch), accumulate with FMAs and combine by a
 // butterfly over the LPR lanes.  No shared memory and no barrier.
 template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
-__global__ void __launch_bounds__(256) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(256, PROLONG ? 1 : 8) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
                                                   const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
   constexpr int GPW = 32 / LPR;  // rows per warp and pass
@@ -571,6 +571,7 @@ int dev_spmv_lo(const DCsr& A, const void* vals, int vt, const float* x, const f
                 const int* w, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
   float* xf = w ? const_cast<float*>(x) : nullptr;
+  if (A.sell && A.sell->v_lo && A.sell->vt == vt) return sell_spmv_lo(*A.sell, x, b, y, mode, w, xf, s);
   if (vt == 2)
     spmv_dispatch<__nv_bfloat16, float>(A.nrows, A.rp, A.ci, (const __nv_bfloat16*)vals, x, b, y, mode, lanes, w, xf, s,
                                         row_batch(A));

@@ -10,6 +10,10 @@
 // near zero (about 1 % on the DG operators).  Each row's entries keep their CSR order and are
 // accumulated with one FMA each from zero, in that order: the result is bitwise the CSR row
 // kernel's.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "airg_common.cuh"
 
 namespace airg {
@@ -22,11 +26,17 @@ constexpr int kSellBuckets = 64;  // row lengths >= 63 share the last bucket (un
 // R FMAs in entry order.  R is a compile-time count so that exactly the slice's width in FP64
 // FMAs is issued: on sm_103a the FP64 pipe takes about 64 cycles per warp instruction, so FMAs
 // issued for entries past the width (predicated off) would cost as much as real ones.
-template <int R, bool PROLONG>
-__device__ __forceinline__ double sell_batch(const int* cs, const double* vs, int k0, const double* x, int nrows,
-                                             const int* __restrict__ w, double s) {
+// One FMA of a stored value (double, float or bf16) with the vector type XT (double or float).
+__device__ __forceinline__ double sfma(double a, double x, double acc) { return fma(a, x, acc); }
+__device__ __forceinline__ float sfma(float a, float x, float acc) { return fmaf(a, x, acc); }
+__device__ __forceinline__ float sfma(__nv_bfloat16 a, float x, float acc) { return fmaf(__bfloat162float(a), x, acc); }
+
+template <int R, bool PROLONG, typename VT, typename XT>
+__device__ __forceinline__ XT sell_batch(const int* cs, const VT* vs, int k0, const XT* x, int nrows,
+                                         const int* __restrict__ w, XT s) {
   int c[R];
-  double a[R], xv[R];
+  VT a[R];
+  XT xv[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     c[t] = __ldcs(cs + (k0 + t) * 32);
@@ -34,11 +44,11 @@ __device__ __forceinline__ double sell_batch(const int* cs, const double* vs, in
   }
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    xv[t] = 0.0;
+    xv[t] = XT(0);
     if (c[t] >= 0) {
       if (PROLONG && c[t] < nrows) {
         const int src = w[c[t]];
-        xv[t] = src >= 0 ? x[nrows + src] : 0.0;
+        xv[t] = src >= 0 ? x[nrows + src] : XT(0);
       } else {
         xv[t] = __ldg(x + c[t]);
       }
@@ -46,7 +56,7 @@ __device__ __forceinline__ double sell_batch(const int* cs, const double* vs, in
   }
 #pragma unroll
   for (int t = 0; t < R; ++t)
-    if (c[t] >= 0) s = fma(a[t], xv[t], s);
+    if (c[t] >= 0) s = sfma(a[t], xv[t], s);
   return s;
 }
 
@@ -55,12 +65,12 @@ __device__ __forceinline__ double sell_batch(const int* cs, const double* vs, in
 // prefetched the next slice's offsets measured 40 % slower), lane l of slice s computes row
 // perm[32 s + l].
 // ------------------------------------------------------------------------------------------
-template <int MODE, bool PROLONG>
+template <int MODE, bool PROLONG, typename VT = double, typename XT = double>
 __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const int* __restrict__ sp,
-                                                   const int* __restrict__ ci, const double* __restrict__ v,
-                                                   const int* __restrict__ perm, const double* x, const double* b,
-                                                   double* y, const int* __restrict__ w, double* xf,
-                                                   const double* __restrict__ coef) {
+                                                   const int* __restrict__ ci, const VT* __restrict__ v,
+                                                   const int* __restrict__ perm, const XT* x, const XT* b,
+                                                   XT* y, const int* __restrict__ w, XT* xf,
+                                                   const XT* __restrict__ coef) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
@@ -68,8 +78,8 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
     const int width = (sp[sl + 1] - beg) >> 5;  // warp-uniform
     const int row = perm[sl * 32 + lane];
     const int* cs = ci + beg + lane;
-    const double* vs = v + beg + lane;
-    double s = 0.0;
+    const VT* vs = v + beg + lane;
+    XT s = XT(0);
     int k0 = 0;
     for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s);
     switch (width - k0) {  // warp-uniform remainder
@@ -83,7 +93,7 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
       default: break;
     }
     if (row >= 0) {
-      double out;
+      XT out;
       if (MODE == SPMV_SET) out = s;
       else if (MODE == SPMV_RESID) out = b[row] - s;
       else if (MODE == SPMV_ADD) out = y[row] + s;
@@ -92,7 +102,7 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
       y[row] = out;
       if (PROLONG) {
         const int src = w[row];
-        xf[row] = src >= 0 ? x[nrows + src] : 0.0;
+        xf[row] = src >= 0 ? x[nrows + src] : XT(0);
       }
     }
   }
@@ -174,12 +184,28 @@ __global__ void k_sell_fill(int nslices, const int* __restrict__ rp, const int* 
   }
 }
 
-template <int MODE, bool PROLONG>
-void launch_sell(const DSell& S, const double* x, const double* b, double* y, const int* w, double* xf,
-                 const double* coef, cudaStream_t s) {
+template <int MODE, bool PROLONG, typename VT, typename XT>
+void launch_sell(const DSell& S, const VT* vals, const XT* x, const XT* b, XT* y, const int* w, XT* xf,
+                 const XT* coef, cudaStream_t s) {
   const int grid = ceil_div(S.nslices, 256 / 32);
-  airg::note_launch(), k_spmv_sell<MODE, PROLONG><<<grid, 256, 0, s>>>(S.nslices, S.nrows, S.sp, S.ci, S.v, S.perm, x, b, y,
-                                                                       w, xf, coef);
+  airg::note_launch(), k_spmv_sell<MODE, PROLONG, VT, XT><<<grid, 256, 0, s>>>(S.nslices, S.nrows, S.sp, S.ci, vals,
+                                                                               S.perm, x, b, y, w, xf, coef);
+}
+
+template <typename VT, typename XT>
+void sell_dispatch(const DSell& S, const VT* vals, const XT* x, const XT* b, XT* y, int mode, const int* w, XT* xf,
+                   const XT* coef, cudaStream_t s) {
+  if (w) {
+    launch_sell<SPMV_RESID, true>(S, vals, x, b, y, w, xf, coef, s);
+    return;
+  }
+  switch (mode) {
+    case SPMV_SET: launch_sell<SPMV_SET, false>(S, vals, x, b, y, w, xf, coef, s); break;
+    case SPMV_RESID: launch_sell<SPMV_RESID, false>(S, vals, x, b, y, w, xf, coef, s); break;
+    case SPMV_ADD: launch_sell<SPMV_ADD, false>(S, vals, x, b, y, w, xf, coef, s); break;
+    case SPMV_AXPB: launch_sell<SPMV_AXPB, false>(S, vals, x, b, y, w, xf, coef, s); break;
+    default: launch_sell<SPMV_ADDB, false>(S, vals, x, b, y, w, xf, coef, s); break;
+  }
 }
 
 }  // namespace
@@ -218,17 +244,42 @@ int build_sell(const DCsr& A, DSell& out, Arena& own, Arena& tmp, cudaStream_t s
 int sell_spmv(const DSell& S, const double* x, const double* b, double* y, int mode, const int* w, double* xf,
               const double* coef, cudaStream_t s) {
   if (S.nslices <= 0) return AIRG_OK;
-  if (w) {
-    launch_sell<SPMV_RESID, true>(S, x, b, y, w, xf, coef, s);
-  } else {
-    switch (mode) {
-      case SPMV_SET: launch_sell<SPMV_SET, false>(S, x, b, y, w, xf, coef, s); break;
-      case SPMV_RESID: launch_sell<SPMV_RESID, false>(S, x, b, y, w, xf, coef, s); break;
-      case SPMV_ADD: launch_sell<SPMV_ADD, false>(S, x, b, y, w, xf, coef, s); break;
-      case SPMV_AXPB: launch_sell<SPMV_AXPB, false>(S, x, b, y, w, xf, coef, s); break;
-      default: launch_sell<SPMV_ADDB, false>(S, x, b, y, w, xf, coef, s); break;
-    }
+  sell_dispatch<double, double>(S, S.v, x, b, y, mode, w, xf, coef, s);
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+__global__ void k_sell_cast(long long n, const double* __restrict__ in, float* __restrict__ outf,
+                            __nv_bfloat16* __restrict__ outb) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (outf) outf[i] = (float)in[i];
+    else outb[i] = __float2bfloat16_rn((float)in[i]);
   }
+}
+
+int sell_cast_values(DSell& S, int vt, Arena& own, cudaStream_t s) {
+  const long long n = std::max(S.nnz_pad, 1LL);
+  if (vt == 1) {
+    float* p;
+    AIRG_TRY(own.alloc(&p, (size_t)n));
+    airg::note_launch(), k_sell_cast<<<grid_for(n, 256), 256, 0, s>>>(S.nnz_pad, S.v, p, nullptr);
+    S.v_lo = p;
+  } else {
+    __nv_bfloat16* p;
+    AIRG_TRY(own.alloc(&p, (size_t)n));
+    airg::note_launch(), k_sell_cast<<<grid_for(n, 256), 256, 0, s>>>(S.nnz_pad, S.v, nullptr, p);
+    S.v_lo = p;
+  }
+  S.vt = vt;
+  KERNEL_CHECK();
+  return AIRG_OK;
+}
+
+int sell_spmv_lo(const DSell& S, const float* x, const float* b, float* y, int mode, const int* w, float* xf,
+                 cudaStream_t s) {
+  if (S.nslices <= 0) return AIRG_OK;
+  if (S.vt == 2) sell_dispatch<__nv_bfloat16, float>(S, (const __nv_bfloat16*)S.v_lo, x, b, y, mode, w, xf, nullptr, s);
+  else sell_dispatch<float, float>(S, (const float*)S.v_lo, x, b, y, mode, w, xf, nullptr, s);
   KERNEL_CHECK();
   return AIRG_OK;
 }

@@ -145,6 +145,25 @@ static int poly_apply_mf(airg_hierarchy* H, const DCsr& A, int lanes, const doub
   return AIRG_OK;
 }
 
+double vcycle_bytes(const airg_hierarchy* H) {
+  const int L = (int)H->lv.size() - 1;
+  const bool mf = H->p.matrix_free != 0;
+  double b = 0.0;
+  for (int l = 0; l < L; ++l) {
+    const SolveLevel& S = H->lv[l];
+    const bool ideal = S.W.nrows > 0;
+    b += S.bytes_Z;
+    if (ideal) b += S.bytes_W;
+    else if (H->p.n_smooth_up == 0) b += (double)S.nf * 16.0;
+    for (int sm = 0; sm < H->p.n_smooth_up; ++sm)
+      b += S.bytes_AF + (sm == 0 && !ideal ? 12.0 * S.nf : 0.0) + (mf ? S.bytes_mf : S.bytes_Ainv);
+  }
+  const SolveLevel& S = H->lv[L];
+  const double inv = mf ? S.bytes_mf : S.bytes_Ainv;
+  b += inv + (double)(H->p.coarse_iters - 1) * (S.bytes_A + inv);
+  return b;
+}
+
 int vcycle_solve_order(airg_hierarchy* H, const double* b0, double* x0) {
   cudaStream_t s = H->s;
   Profiler& P = H->prof;
@@ -315,7 +334,10 @@ static int ensure_vgraph(airg_hierarchy* H) {
 }
 
 int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0) {
-  if (!H->use_graph && !H->vt) return vcycle_solve_order(H, b0, x0);
+  if (!H->use_graph && !H->vt) {
+    ProfScope pv(H->prof, H->s, PC_VCYCLE, H->bytes_V);
+    return vcycle_solve_order(H, b0, x0);
+  }
   AIRG_TRY(ensure_vgraph(H));
   if (H->vt) {  // FP64 in, float V-cycle, FP64 out
     if (H->prof.graph_unread) {
@@ -323,7 +345,10 @@ int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0) {
       prof_graph_read(H);
     }
     dev_cast_d2f(b0, H->gin_f, H->n0, H->s);
-    CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+    {
+      ProfScope pv(H->prof, H->s, PC_VCYCLE, H->bytes_V);
+      CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+    }
     g_launches.fetch_add(H->vg_kernels);
     if (!H->prof.graph_recs.empty()) H->prof.graph_unread = 1;
     dev_cast_f2d(H->gout_f, x0, H->n0, H->s);
@@ -336,7 +361,10 @@ int vcycle_apply(airg_hierarchy* H, const double* b0, double* x0) {
     prof_graph_read(H);
   }
   CU_TRY(cudaMemcpyAsync(H->gin, b0, bytes, cudaMemcpyDeviceToDevice, H->s));
-  CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+  {
+    ProfScope pv(H->prof, H->s, PC_VCYCLE, H->bytes_V);
+    CU_TRY(cudaGraphLaunch(H->vg_exec, H->s));
+  }
   g_launches.fetch_add(H->vg_kernels);
   if (!H->prof.graph_recs.empty()) H->prof.graph_unread = 1;
   CU_TRY(cudaMemcpyAsync(x0, H->gout, bytes, cudaMemcpyDeviceToDevice, H->s));

@@ -156,3 +156,34 @@ def test_adjoint_gradients_match_oracle_dense_solve():
     assert J == pytest.approx(w_np @ u, rel=1e-10)
     np.testing.assert_allclose(gs, gs_ref, rtol=1e-8, atol=1e-12 * np.abs(gs_ref).max())
     np.testing.assert_allclose(gq, gq_ref, rtol=1e-8, atol=1e-12 * np.abs(gq_ref).max())
+
+
+def test_cached_hierarchies_are_reused_while_the_matrix_is_unchanged():
+    # the adjoint form's cache keeps the hierarchies of A and A^T: right-hand sides that change
+    # (the source q) re-use them, and the gradients are bitwise those of fresh setups; writing to
+    # the matrix's values builds new ones
+    p = P.adjoint_2d(32)
+    rp, ci, v = dev(p.rowptr, p.col, p.val)
+    w = torch.from_numpy(np.random.default_rng(7).standard_normal(p.n)).cuda()
+    cache = airg.HierarchyCache()
+    Fc, Fn = airg.solve_fn(cache), airg.solve_fn()
+    grads, held = [], []
+    for q in (1.0, 2.0, 0.5):
+        out = []
+        for F in (Fc, Fn):
+            vv = v.detach().clone().requires_grad_(True) if F is Fn else v.requires_grad_(True)
+            bb = (q * torch.from_numpy(p.b).cuda()).requires_grad_(True)
+            x = F.apply(rp, ci, vv, bb, airg.Params(), 1e-10)
+            (w * x).sum().backward()
+            out.append((vv.grad.clone(), bb.grad.clone()))
+            vv.grad = None
+        grads.append(out)
+        held.append((cache.entries[False][1], cache.entries[True][1]))
+    for (gc, gn) in grads:
+        assert torch.equal(gc[0], gn[0]) and torch.equal(gc[1], gn[1])
+    assert all(h[0] is held[0][0] and h[1] is held[0][1] for h in held)  # built once, re-used twice
+    with torch.no_grad():
+        v.mul_(1.0)  # a write: the version counter moves, so the next call sets up again
+    x = Fc.apply(rp, ci, v, torch.from_numpy(p.b).cuda(), airg.Params(), 1e-10)
+    assert cache.entries[False][1] is not held[0][0]
+    cache.clear()
