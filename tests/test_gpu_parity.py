@@ -392,6 +392,38 @@ def test_setup_reuse_with_strength_zero_is_a_fresh_setup():
     assert torch.equal(xf, xr)
 
 
+def test_setup_reuse_across_directions():
+    # directions of one mesh that share the upwind pattern (unjittered cells, angles inside one
+    # 45-degree sector): with strength 0 the re-used level-0 splitting of another direction is the
+    # one a fresh setup computes, so the solve is bitwise the fresh one; with the default strength
+    # the template direction's splittings on every level give the oracle's hierarchy with the same
+    # forced splittings
+    ds = P.directions_2d(64)
+    b = torch.from_numpy(ds[3].b).cuda()
+    par0 = airg.Params(strong_threshold=0.0)
+    T0 = airg.Hierarchy(*dev(ds[0]), par0)
+    Hf = airg.Hierarchy(*dev(ds[3]), par0)
+    Hr = airg.Hierarchy(*dev(ds[3]), par0, reuse=T0, reuse_levels=1)
+    xf, i_f = Hf.solve(b, rtol=1e-10)
+    xr, i_r = Hr.solve(b, rtol=1e-10)
+    assert i_f["status"] == 0 and i_f["iters"] == i_r["iters"]
+    assert torch.equal(xf, xr)
+    op = O.Params()
+    T = airg.Hierarchy(*dev(ds[0]), gpu_params(op))
+    cf = [T.vectors(l)["cf"] for l in range(T.num_levels - 1)]
+    g = ds[2]
+    Hd = airg.Hierarchy(*dev(g), gpu_params(op), reuse=T)
+    Ho = O.Hierarchy(g.rowptr, g.col, g.val, op, cf=cf)
+    assert_csr_close(Ho.export(0, "Z"), Hd.export(0, "Z"), what="Z")
+    assert_csr_close(Ho.export(1, "A"), Hd.export(1, "A"), what="A_c")
+    xo, io = Ho.solve(g.b, rtol=1e-12, max_it=300)
+    xg, ig = Hd.solve(torch.from_numpy(g.b).cuda(), rtol=1e-12, max_it=300)
+    assert ig["status"] == 0 and io["status"] == 0
+    xg = xg.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    assert abs(ig["iters"] - io["iters"]) <= 1
+
+
 def test_polynomial_order_trend():
     """Section "GMRES polynomial order" (table of orders 1-6): with first-order fixed sparsity the
     iteration count falls steeply from order 1 and flattens by order 4-6."""
@@ -470,6 +502,27 @@ def test_setup_is_deterministic_run_to_run():
     x1, i1 = H1.solve(b, rtol=1e-10)
     x2, i2 = H2.solve(b, rtol=1e-10)
     assert i1 == i2 and torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_sliced_ell_and_csr_agree_bitwise(monkeypatch, prec):
+    # the float / bf16-value V-cycle reads the large residual operators from their sliced ELL copy
+    # (values cast element by element, as for the CSR copy) and sums each row in CSR order with
+    # fmaf from zero: V-cycles and solves are bitwise those of the CSR kernels
+    p = P.blocked_sigma_2d(150)
+    b = torch.from_numpy(p.b).cuda()
+    par = airg.Params(precision=prec)
+    Hs = airg.Hierarchy(*dev(p), par)
+    assert Hs.level_info(0)["sell_mask"] & 1
+    ys = Hs.vcycle(b)
+    xs, is_ = Hs.solve(b, rtol=1e-10)
+    monkeypatch.setenv("AIRG_NO_SELL", "1")
+    Hc = airg.Hierarchy(*dev(p), par)
+    assert Hc.level_info(0)["sell_mask"] == 0
+    yc = Hc.vcycle(b)
+    xc, ic = Hc.solve(b, rtol=1e-10)
+    assert torch.equal(ys, yc)
+    assert is_["iters"] == ic["iters"] and torch.equal(xs, xc)
 
 
 @pytest.mark.parametrize("mesh,variant", [(160, {}), (160, {"matrix_free": 1}), (160, {"ideal_prolong": 1}),
