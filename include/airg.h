@@ -186,8 +186,9 @@ int airg_solve_batched(airg_batch* B, const double* const* b, double* const* x, 
                        airg_solve_info* infos, airg_stream_t stream);
 void airg_batch_free(airg_batch* B);
 
-/* The batched form's SpMV autotuner.  airg_batch_create times every lanes-per-row variant (1, 2, 4,
- * ..., 32 lanes per row) of each grouped operator with at least 16384 rows and keeps the fastest;
+/* The batched form's SpMV autotuner.  airg_batch_create times the row-length rule's lanes per row
+ * and its two neighbours (half and twice as many, within 1..32) on each grouped operator with at
+ * least 16384 rows and keeps the fastest;
  * smaller groups keep the row-length rule.  Setting the environment variable AIRG_NO_AUTOTUNE=1
  * keeps the rule everywhere.  The variants sum a row in different orders, so the chosen variants
  * can change results in the last bits.  airg_batch_tuned writes, for the first `cap` tuned groups,

@@ -25,18 +25,37 @@ struct Group {
   int lanes = 1;
 };
 
-// row r of the output = row (r - r0) of a source operator; columns transformed
-__global__ void k_concat_rows(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                              const double* __restrict__ v, int row0, int nnz0, int col_off, int* __restrict__ orp,
-                              int* __restrict__ oci, double* __restrict__ ov, int* __restrict__ map, int map_off) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += (long long)gridDim.x * blockDim.x) {
-    const int b = rp[i], e = rp[i + 1];
-    orp[row0 + i] = nnz0 + b;
-    for (int k = b; k < e; ++k) {
-      oci[nnz0 + k] = ci[k] + col_off;
-      ov[nnz0 + k] = v[k];
+// Concatenation of all parts of a group in one launch: part p's rows go to rows r0_p.. of the
+// group, its entries to z0_p.., its columns shifted by col_off_p; map[r] = map_off_p + local row.
+// The part of a row is found by a binary search over the parts' first rows (parts with rows only).
+struct ConcatPart {
+  const int* rp;
+  const int* ci;
+  const double* v;
+  int r0, z0, col_off, map_off, nrows;
+};
+__global__ void k_concat_parts(const ConcatPart* __restrict__ parts, int nparts, int rows, int nnz_total,
+                               int* __restrict__ orp, int* __restrict__ oci, double* __restrict__ ov,
+                               int* __restrict__ map) {
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0) orp[rows] = nnz_total;
+  for (long long rr = t0; rr < rows; rr += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)rr;
+    int lo = 0, hi = nparts - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (parts[mid].r0 <= r) lo = mid;
+      else hi = mid - 1;
     }
-    if (map) map[row0 + i] = map_off + (int)i;
+    const ConcatPart& P = parts[lo];
+    const int i = r - P.r0;
+    const int b = P.rp[i], e = P.rp[i + 1];
+    orp[r] = P.z0 + b;
+    for (int k = b; k < e; ++k) {
+      oci[P.z0 + k] = P.ci[k] + P.col_off;
+      ov[P.z0 + k] = P.v[k];
+    }
+    if (map) map[r] = P.map_off + i;
   }
 }
 
@@ -242,6 +261,7 @@ using namespace airg;
 
 struct airg_batch {
   int nsys = 0;
+  std::deque<std::vector<airg::ConcatPart>> part_tables;  // host tables of the concatenation launches
   cudaStream_t s = nullptr;
   Arena mem;
   std::vector<airg_hierarchy*> H;
@@ -269,14 +289,15 @@ struct airg_batch {
 
 namespace {
 
-// The autotuner: every lanes-per-row variant of the grouped SpMV (1, 2, 4, ..., 32) runs on the
-// group's operator (SET into scratch vectors, one untimed launch then kTuneReps timed with CUDA
-// events on the batch's stream), and the fastest is kept.  Groups below kTuneMinRows rows keep the
+// The autotuner: the row-length rule's lanes per row and its two neighbours (half and twice as
+// many lanes) run on the group's operator (SET into scratch vectors, one untimed launch then
+// kTuneReps timed with CUDA events on the batch's stream), and the fastest is kept.  Three
+// candidates rather than all six keep the creation of a batch cheap next to its solves.  Groups below kTuneMinRows rows keep the
 // row-length rule: their launches are latency-bound whatever the variant.  The row sums of
 // different variants round differently, so a batch's results can change in the last bits with the
 // variants chosen.
 constexpr long long kTuneMinRows = 16384;
-constexpr int kTuneReps = 3;
+constexpr int kTuneReps = 2;
 
 int tune_lanes(airg_batch* B, Group& g) {
   cudaStream_t s = B->s;
@@ -295,7 +316,11 @@ int tune_lanes(airg_batch* B, Group& g) {
   int best = rule;
   float best_ms = 0.f;
   int rc = AIRG_OK;
-  for (int lanes = 1; lanes <= 32 && rc == AIRG_OK; lanes *= 2) {
+  // the row-length rule's choice and its two neighbours (half and twice the lanes per row)
+  const int cand[3] = {rule, rule / 2, rule * 2};
+  for (int c = 0; c < 3 && rc == AIRG_OK; ++c) {
+    const int lanes = cand[c];
+    if (lanes < 1 || lanes > 32) continue;
     g.lanes = lanes;
     rc = spmv_mapped(g, B->tx, nullptr, B->ty, SPMV_SET, s);
     if (rc == AIRG_OK) rc = cuda_status(cudaEventRecord(e0, s));
@@ -304,7 +329,7 @@ int tune_lanes(airg_batch* B, Group& g) {
     if (rc == AIRG_OK) rc = cuda_status(cudaEventSynchronize(e1));
     float ms = 0.f;
     if (rc == AIRG_OK) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
-    if (rc == AIRG_OK && (lanes == 1 || ms < best_ms)) {
+    if (rc == AIRG_OK && (c == 0 || ms < best_ms)) {
       best_ms = ms;
       best = lanes;
     }
@@ -328,19 +353,21 @@ int concat_group(airg_batch* B, std::vector<std::pair<int, const DCsr*>>& parts,
   if (rows > 0x7fffffffLL || nnz > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
   AIRG_TRY(B->mem.csr(g.A, (int)rows, (int)B->N, (int)nnz));
   AIRG_TRY(B->mem.alloc(&g.map, (size_t)rows));
+  // one launch per group; the part table stays alive on the host until the build synchronises
+  B->part_tables.emplace_back();
+  std::vector<ConcatPart>& tab = B->part_tables.back();
   long long r0 = 0, z0 = 0;
   for (size_t q = 0; q < parts.size(); ++q) {
     const DCsr& M = *parts[q].second;
-    if (M.nrows > 0)
-      airg::note_launch(), k_concat_rows<<<grid_for(M.nrows, 256), 256, 0, s>>>(M.nrows, M.rp, M.ci, M.v, (int)r0, (int)z0,
-                                                                               col_off[q], g.A.rp, g.A.ci, g.A.v, g.map,
-                                                                               map_off[q]);
+    if (M.nrows > 0) tab.push_back({M.rp, M.ci, M.v, (int)r0, (int)z0, col_off[q], map_off[q], M.nrows});
     r0 += M.nrows;
     z0 += M.nnz;
   }
-  const int last = (int)nnz;
-  CU_TRY(cudaMemcpyAsync(g.A.rp + rows, &last, sizeof(int), cudaMemcpyHostToDevice, s));
-  CU_TRY(cudaStreamSynchronize(s));  // `last` lives on the host stack
+  ConcatPart* dtab;
+  AIRG_TRY(B->mem.alloc(&dtab, tab.size()));
+  CU_TRY(cudaMemcpyAsync(dtab, tab.data(), sizeof(ConcatPart) * tab.size(), cudaMemcpyHostToDevice, s));
+  airg::note_launch(), k_concat_parts<<<grid_for(rows, 256), 256, 0, s>>>(dtab, (int)tab.size(), (int)rows, (int)nnz,
+                                                                           g.A.rp, g.A.ci, g.A.v, g.map);
   g.lanes = pick_lanes((double)nnz / (double)rows);
   KERNEL_CHECK();
   if (B->tune && rows >= kTuneMinRows) AIRG_TRY(tune_lanes(B, g));

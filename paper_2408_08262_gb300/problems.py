@@ -412,5 +412,18 @@ def groups_2d(mesh_n: int = 512, ngroups: int = 4, theta: float = 0.3, config_in
             for g in range(ngroups)]
 
 
+def directions_2d(mesh_n: int = 512, thetas=(0.15, 0.35, 0.55, 0.75), config_index: int = 6) -> list[Problem]:
+    """Directions of one mesh whose upwind couplings coincide: the square cells are not jittered, so
+    every edge is horizontal, vertical or on a +-45 degree diagonal, and any two directions strictly
+    inside one 45-degree sector (here (0, pi/4)) see the same inflow edges; the matrices share their
+    sparsity pattern and differ in values.  sigma = 1, q = 1 (the setup re-use workload across
+    directions)."""
+    seed = derive_seed(config_index, 0)
+    for th in thetas:
+        if not 0.0 < th < math.pi / 4:
+            raise ValueError("directions must lie strictly inside (0, pi/4)")
+    return [p1_dg_2d(mesh_n, float(th), sigma=1.0, q=1.0, seed=seed, jitter=0.0) for th in thetas]
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(n)

@@ -80,3 +80,26 @@ def test_batched_autotuner_picks_lanes_and_keeps_the_solution(monkeypatch):
     for x, i, y, j in zip(xs, infos, xr, ir):
         assert i["status"] == 0 and j["status"] == 0 and abs(i["iters"] - j["iters"]) <= 1
         assert (torch.linalg.norm(x - y) / torch.linalg.norm(y)).item() <= 1e-10
+
+
+def test_batched_at_the_full_system_sizes():
+    # the largest and smallest member sizes of the 64-system batch (512^2: 1,572,864 DOFs; 64^2:
+    # 24,576 DOFs) in one batch, with the default parameters (automatic truncation): each against
+    # its individual solve, the small one also against the oracle
+    ps = [P.p1_dg_2d(512, 2.2, sigma=1.7, seed=2001), P.p1_dg_2d(64, 4.1, sigma=0.4, seed=2002)]
+    par = airg.Params()
+    Hs = [airg.Hierarchy(*dev(p), par) for p in ps]
+    bs = [torch.from_numpy(p.b).cuda() for p in ps]
+    B = airg.Batch(Hs)
+    xs, infos = B.solve(bs, rtol=1e-12, max_it=300)
+    for p, H, b, x, info in zip(ps, Hs, bs, xs, infos):
+        xi, ii = H.solve(b, rtol=1e-12, max_it=300)
+        assert info["status"] == 0 and ii["status"] == 0 and info["relres"] <= 1e-12
+        assert abs(info["iters"] - ii["iters"]) <= 1
+        assert (torch.linalg.norm(x - xi) / torch.linalg.norm(xi)).item() <= 1e-10
+    q = ps[1]
+    Ho = O.Hierarchy(q.rowptr, q.col, q.val, O.Params(coarse_size=max(64, min(60000, q.n // 16))))
+    xo, io = Ho.solve(q.b, rtol=1e-12, max_it=300)
+    assert io["status"] == 0
+    assert np.linalg.norm(xs[1].cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-10
+    B.close()

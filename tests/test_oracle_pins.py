@@ -736,6 +736,33 @@ def test_reused_splittings_give_a_convergent_solver():
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
 
 
+def test_directions_of_one_sector_share_the_pattern_and_the_strength_zero_splitting():
+    # directions across a mesh (Sections "Strong tolerances" and "Conclusions": the splitting at
+    # strength 0 does not depend on the angle): on the unjittered mesh every edge is horizontal,
+    # vertical or diagonal, so directions inside (0, pi/4) see the same inflow edges.  The patterns
+    # coincide (a direction in another sector has another pattern), the values differ, the strength-0
+    # splittings are identical, and another direction's splittings on every level still solve to the
+    # dense LU solution
+    ds = P.directions_2d(12, thetas=(0.1, 0.4, 0.7))
+    for d in ds[1:]:
+        assert np.array_equal(d.rowptr, ds[0].rowptr) and np.array_equal(d.col, ds[0].col)
+        assert not np.array_equal(d.val, ds[0].val)
+    other = P.p1_dg_2d(12, 1.2, sigma=1.0, q=1.0, seed=ds[0].meta["seed"], jitter=0.0)
+    assert not (np.array_equal(other.rowptr, ds[0].rowptr) and np.array_equal(other.col, ds[0].col))
+    par0 = O.Params(strong_threshold=0.0)
+    cfs = [O.cf_split(d.rowptr, d.col, d.val, par0)["cf"] for d in ds]
+    assert all(np.array_equal(c, cfs[0]) for c in cfs)
+    par = O.Params(coarse_size=16)
+    T = O.Hierarchy(ds[0].rowptr, ds[0].col, ds[0].val, par)
+    cf = [T.vectors(l)["cf"] for l in range(T.num_levels - 1)]
+    g = ds[2]
+    H = O.Hierarchy(g.rowptr, g.col, g.val, par, cf=cf)
+    xs = O.dense_solve(g.rowptr, g.col, g.val, g.b)
+    x, info = H.solve(g.b, rtol=1e-12, max_it=300)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10
+
+
 def test_matrix_free_airg_solution_matches_dense_lu():
     p = P.streaming_2d(16)
     xs = O.dense_solve(p.rowptr, p.col, p.val, p.b)
