@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256, (kRowBatch == 4 && !PROLONG) ? 8 : 1) k_s
 // lane l taking entries l, l + LPR, ... (4 per batch), accumulate with FMAs and combine by a
 // butterfly over the LPR lanes.  No shared memory and no barrier.
 template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
-__global__ void __launch_bounds__(256, PROLONG ? 1 : 8) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(256, PROLONG ? 6 : 8) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                   const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
                                                   const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
   constexpr int GPW = 32 / LPR;  // rows per warp and pass

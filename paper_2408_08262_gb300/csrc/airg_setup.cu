@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "airg_common.cuh"
@@ -1264,6 +1265,52 @@ __device__ void bitonic_sort_kv(int* a, double* v, int P, int t) {
     }
 }
 
+// Writes the kept entries of a warp's compacted row (key/val[0..u), u <= 32*NE) in column order:
+// a kept entry's position is the number of kept columns below it (dropped entries take the key
+// 0x7fffffff, which is below no kept column).  Returns the number kept.
+template <int NE>
+__device__ __forceinline__ int spg_rank_write(const SpgArgs& g, int* key, const double* val, int u, long long thr,
+                                              int i, long long o, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  int mk[NE];
+  double mv[NE];
+  int kept = 0;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int t = lane + 32 * e;
+    int j = 0x7fffffff;
+    double c = 0.0;
+    if (t < u) {
+      j = key[t];
+      c = val[t];
+      if (!(abs_bits(c) >= thr || (g.keep_diag && j == i))) j = 0x7fffffff;
+    }
+    mk[e] = j;
+    mv[e] = c;
+    kept += __popc(__ballot_sync(FULL, j != 0x7fffffff));
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+    if (lane + 32 * e < u) key[lane + 32 * e] = mk[e];
+  __syncwarp();
+  int rk[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) rk[e] = 0;
+  for (int t = 0; t < u; ++t) {
+    const int kt = key[t];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) rk[e] += (kt < mk[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+    if (mk[e] != 0x7fffffff) {
+      g.tcol[o + rk[e]] = mk[e];
+      g.tval[o + rk[e]] = mv[e];
+    }
+  return kept;
+}
+
 template <int CAP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int* __restrict__ rows,
                                                             const int* __restrict__ nrows_dev, int* next_rows,
@@ -1333,12 +1380,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
     for (int s2 = 16; s2 > 0; s2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
     const long long thr = spg_thr(g, mx);
     const long long o = g.ubo[i];
-    int P = 32;
-    while (P < u) P <<= 1;
-    for (int t = u + lane; t < P; t += 32) { key[t] = 0x7fffffff; val[t] = 0.0; }
-    __syncwarp();
-    bitonic_sort_kv<32>(key, val, P, lane);
-    int outc = 0;
+    // drop first (the threshold is known), so that only the kept entries are ordered
+    int u2 = 0;
     for (int base = 0; base < u; base += 32) {
       const int t = base + lane;
       int j = 0;
@@ -1350,63 +1393,36 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
         keep = abs_bits(c) >= thr || (g.keep_diag && j == i);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
       if (keep) {
-        const int d = outc + __popc(bal & ((1u << lane) - 1u));
-        g.tcol[o + d] = j;
-        g.tval[o + d] = c;
+        const int d = u2 + __popc(bal & ((1u << lane) - 1u));
+        key[d] = j;
+        val[d] = c;
       }
-      outc += __popc(bal);
+      u2 += __popc(bal);
+      __syncwarp();
     }
-    if (lane == 0) g.cnt[i] = outc;
+    if (u2 <= 256) {  // position = rank among the kept columns (every entry kept: threshold 0)
+      if (u2 <= 32) spg_rank_write<1>(g, key, val, u2, 0, i, o, lane);
+      else if (u2 <= 64) spg_rank_write<2>(g, key, val, u2, 0, i, o, lane);
+      else if (u2 <= 128) spg_rank_write<4>(g, key, val, u2, 0, i, o, lane);
+      else spg_rank_write<8>(g, key, val, u2, 0, i, o, lane);
+    } else {
+      int P = 32;
+      while (P < u2) P <<= 1;
+      for (int t = u2 + lane; t < P; t += 32) { key[t] = 0x7fffffff; val[t] = 0.0; }
+      __syncwarp();
+      bitonic_sort_kv<32>(key, val, P, lane);
+      for (int t = lane; t < u2; t += 32) {
+        g.tcol[o + t] = key[t];
+        g.tval[o + t] = val[t];
+      }
+    }
+    if (lane == 0) g.cnt[i] = u2;
     __syncwarp();
   }
 }
 
-// Writes the kept entries of a warp's compacted row (key/val[0..u), u <= 32*NE) in column order:
-// a kept entry's position is the number of kept columns below it (dropped entries take the key
-// 0x7fffffff, which is below no kept column).  Returns the number kept.
-template <int NE>
-__device__ __forceinline__ int spg_rank_write(const SpgArgs& g, int* key, const double* val, int u, long long thr,
-                                              int i, long long o, int lane) {
-  constexpr unsigned FULL = 0xffffffffu;
-  int mk[NE];
-  double mv[NE];
-  int kept = 0;
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    const int t = lane + 32 * e;
-    int j = 0x7fffffff;
-    double c = 0.0;
-    if (t < u) {
-      j = key[t];
-      c = val[t];
-      if (!(abs_bits(c) >= thr || (g.keep_diag && j == i))) j = 0x7fffffff;
-    }
-    mk[e] = j;
-    mv[e] = c;
-    kept += __popc(__ballot_sync(FULL, j != 0x7fffffff));
-  }
-  __syncwarp();
-#pragma unroll
-  for (int e = 0; e < NE; ++e)
-    if (lane + 32 * e < u) key[lane + 32 * e] = mk[e];
-  __syncwarp();
-  int rk[NE];
-#pragma unroll
-  for (int e = 0; e < NE; ++e) rk[e] = 0;
-  for (int t = 0; t < u; ++t) {
-    const int kt = key[t];
-#pragma unroll
-    for (int e = 0; e < NE; ++e) rk[e] += (kt < mk[e]);
-  }
-#pragma unroll
-  for (int e = 0; e < NE; ++e)
-    if (mk[e] != 0x7fffffff) {
-      g.tcol[o + rk[e]] = mk[e];
-      g.tval[o + rk[e]] = mv[e];
-    }
-  return kept;
-}
 
 // Medium rows, staged: one warp per row with at most kStageCap candidates and kStageA entries in A's
 // row.  The row's A entries (value, B row start, candidate offset) and then all of its candidates
@@ -1637,6 +1653,168 @@ __global__ void __launch_bounds__(256) k_spgemm_block(SpgArgs g, const int* __re
   }
 }
 
+// Block-wide exclusive scan of one int per thread (256 threads); *total receives the sum.
+__device__ __forceinline__ int esc_block_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  int before = 0, all = 0;
+  for (int q = 0; q < 8; ++q) {
+    if (q < wid) before += wsum[q];
+    all += wsum[q];
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - v;
+}
+
+// Long rows (kWarpCap < candidates <= kEscCap, two tiers: 2048 and 4096): one 256-thread CTA per row, expand - sort -
+// compress.  Every candidate (column j, A entry e, B value) gets a slot in the order A entries
+// ascending, each B row ascending; the 64-bit keys j << 32 | slot are sorted (bitonic, in shared
+// memory), so each column's candidates sit together in arrival order, and one thread folds each
+// run with fma from zero: per output the same ascending-l chain as every other path, hence the
+// same bits.  The scaled outputs are dropped against the row's threshold and written in column
+// order.  Rows with more candidates or A entries than the shared arrays hold go to `rest_rows`
+// (the per-column block kernel).
+template <int kEscCap>
+constexpr size_t esc_smem() { return (size_t)kEscCap * (8 + 8 + 4 + 4 + 8) + (size_t)(kEscCap / 2 + 1) * 4; }
+
+template <int kEscCap>
+__global__ void __launch_bounds__(256) k_spgemm_esc(SpgArgs g, const int* __restrict__ rows,
+                                                    const int* __restrict__ nrows_dev, int* rest_rows, int* n_rest) {
+  constexpr int kEscMaxA = kEscCap / 2;
+  extern __shared__ __align__(16) unsigned char esm[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(esm);
+  double* bvs = reinterpret_cast<double*>(key + kEscCap);
+  double* oval = bvs + kEscCap;
+  int* kid = reinterpret_cast<int*>(oval + kEscCap);
+  int* ocol = kid + kEscCap;
+  int* start = ocol + kEscCap;
+  __shared__ int wsum[8];
+  __shared__ long long wmx[8];
+  const int t0 = threadIdx.x, lane = t0 & 31, wid = t0 >> 5;
+  const int nrows = *nrows_dev;
+  for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+    const int i = rows[rr];
+    const long long ub = g.ubo[i + 1] - g.ubo[i];
+    const int ab = g.arp[i], ae = g.arp[i + 1], na = ae - ab;
+    if (ub > kEscCap || na > kEscMaxA) {
+      if (t0 == 0) rest_rows[atomicAdd(n_rest, 1)] = i;
+      continue;
+    }
+    // slot offsets of the A entries: exclusive scan of their B row lengths
+    int carry = 0;
+    for (int base = 0; base < na; base += 256) {
+      const int e = base + t0;
+      int len = 0;
+      if (e < na) {
+        int b0, b1;
+        spg_brow(g, g.aci[ab + e], b0, b1);
+        len = b1 - b0;
+      }
+      int tot;
+      const int ex = esc_block_scan(len, wsum, &tot);
+      if (e < na) start[e] = carry + ex;
+      carry += tot;
+    }
+    if (t0 == 0) start[na] = carry;
+    int P = 256;
+    while (P < ub) P <<= 1;
+    __syncthreads();
+    // expansion: slot s belongs to the last A entry whose start is <= s
+    for (int sl = t0; sl < P; sl += 256) {
+      if (sl < ub) {
+        int lo = 0, hi = na - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (start[mid] <= sl) lo = mid;
+          else hi = mid - 1;
+        }
+        int b0, b1;
+        spg_brow(g, g.aci[ab + lo], b0, b1);
+        const int q = b0 + (sl - start[lo]);
+        key[sl] = ((unsigned long long)(unsigned)g.bci[q] << 32) | (unsigned)sl;
+        bvs[sl] = g.bv[q];
+        kid[sl] = lo;
+      } else {
+        key[sl] = ~0ull;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int idx = t0; idx < P; idx += 256) {
+          const int ixj = idx ^ j;
+          if (ixj > idx) {
+            const unsigned long long x = key[idx], y = key[ixj];
+            if ((x > y) == ((idx & k) == 0)) {
+              key[idx] = y;
+              key[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // runs of one column -> outputs, numbered in column order
+    int nout = 0;
+    long long mx = 0;
+    for (int base = 0; base < (int)ub; base += 256) {
+      const int p = base + t0;
+      bool head = false;
+      if (p < ub) head = (p == 0) || ((key[p] >> 32) != (key[p - 1] >> 32));
+      int tot;
+      const int oi = nout + esc_block_scan(head ? 1 : 0, wsum, &tot);
+      if (head) {
+        const unsigned long long jj = key[p] >> 32;
+        double acc = 0.0;
+        for (int pp = p; pp < ub && (key[pp] >> 32) == jj; ++pp) {
+          const int sl = (int)(key[pp] & 0xffffffffu);
+          acc = fma(g.av[ab + kid[sl]], bvs[sl], acc);
+        }
+        const double c = spg_scale(g, acc);
+        ocol[oi] = (int)jj;
+        oval[oi] = c;
+        mx = max(mx, abs_bits(c));
+      }
+      nout += tot;
+    }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+    if (lane == 0) wmx[wid] = mx;
+    __syncthreads();
+    mx = 0;
+    for (int q = 0; q < 8; ++q) mx = max(mx, wmx[q]);
+    const long long thr = spg_thr(g, mx);
+    const long long o = g.ubo[i];
+    int outc = 0;
+    for (int base = 0; base < nout; base += 256) {
+      const int t = base + t0;
+      bool keep = false;
+      int j = 0;
+      double c = 0.0;
+      if (t < nout) {
+        j = ocol[t];
+        c = oval[t];
+        keep = abs_bits(c) >= thr || (g.keep_diag && j == i);
+      }
+      int tot;
+      const int d = outc + esc_block_scan(keep ? 1 : 0, wsum, &tot);
+      if (keep) {
+        g.tcol[o + d] = j;
+        g.tval[o + d] = c;
+      }
+      outc += tot;
+    }
+    if (t0 == 0) g.cnt[i] = outc;
+    __syncthreads();
+  }
+}
+
 // Compaction of the per-row results (at the candidate offsets ubo) into CSR: a CTA takes 256
 // consecutive rows, whose output is one contiguous range; each thread finds its entry's row by
 // binary search over the CTA's row starts in shared memory, so the writes are coalesced.
@@ -1697,13 +1875,16 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
   AIRG_TRY(tmp.alloc(&g.tcol, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.tval, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.cnt, std::max(ar, 1)));
-  // row lists of the wider paths; counters: [0] mid, [1] big, [2] long, [3] error
-  int *mid, *big, *lng, *ctr;
+  // row lists of the wider paths; counters: [0] mid, [1] big, [2] long, [3] error, [6] longest,
+  // [7] rows past the first expand-sort tier
+  int *mid, *big, *lng, *rest, *rest2, *ctr;
+  AIRG_TRY(tmp.alloc(&rest2, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&mid, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&big, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&lng, std::max(ar, 1)));
-  AIRG_TRY(tmp.alloc(&ctr, 4));
-  CU_TRY(cudaMemsetAsync(ctr, 0, 4 * sizeof(int), s));
+  AIRG_TRY(tmp.alloc(&rest, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&ctr, 8));
+  CU_TRY(cudaMemsetAsync(ctr, 0, 8 * sizeof(int), s));
   if (ar > 0) {
     airg::note_launch(), k_spgemm_thread<<<grid_for(ar, 128, 152 * 64), 128, 0, s>>>(g, mid, ctr + 0);
     static bool stage_set = false;
@@ -1714,13 +1895,30 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
     }
     airg::note_launch(), k_spgemm_warp_staged<<<152 * 3, kStageWarps * 32, stage_smem, s>>>(g, mid, ctr + 0, big, ctr + 1);
     airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2);
+    static bool esc_set = false;
+    if (!esc_set) {
+      CU_TRY(cudaFuncSetAttribute(k_spgemm_esc<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esc_smem<2048>()));
+      CU_TRY(cudaFuncSetAttribute(k_spgemm_esc<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esc_smem<4096>()));
+      esc_set = true;
+    }
+    // AIRG_SPGEMM_NO_ESC=1 sends every long row to the per-column block kernel (same results)
+    const char* no_esc_env = getenv("AIRG_SPGEMM_NO_ESC");
+    const bool no_esc = no_esc_env && no_esc_env[0] == '1';
+    const int* blk_rows = lng;
+    const int* blk_n = ctr + 2;
+    if (!no_esc) {
+      airg::note_launch(), k_spgemm_esc<2048><<<152 * 3, 256, esc_smem<2048>(), s>>>(g, lng, ctr + 2, rest2, ctr + 7);
+      airg::note_launch(), k_spgemm_esc<4096><<<152, 256, esc_smem<4096>(), s>>>(g, rest2, ctr + 7, rest, ctr + 6);
+      blk_rows = rest;
+      blk_n = ctr + 6;
+    }
     static bool smem_set = false;
     const size_t smem = sizeof(int) * (size_t)kBlockCapMax;
     if (!smem_set) {
       CU_TRY(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       smem_set = true;
     }
-    airg::note_launch(), k_spgemm_block<<<152, 256, smem, s>>>(g, lng, ctr + 2, kBlockCapMax, ctr + 3);
+    airg::note_launch(), k_spgemm_block<<<152, 256, smem, s>>>(g, blk_rows, blk_n, kBlockCapMax, ctr + 3);
     KERNEL_CHECK();
   }
   out.nrows = ar;

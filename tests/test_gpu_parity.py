@@ -504,6 +504,23 @@ def test_setup_is_deterministic_run_to_run():
     assert i1 == i2 and torch.equal(x1, x2)
 
 
+def test_expand_sort_products_equal_the_per_column_products(monkeypatch):
+    # product rows of more than 1024 candidates (the coarse 3D levels) are formed by expand - sort -
+    # compress in one CTA; each output keeps the ascending-l fma chain, so every level's operators
+    # are bitwise those of the per-column block kernel
+    p = P.kuhn_3d(48)
+    par = airg.Params(keep_setup=1)
+    He = airg.Hierarchy(*dev(p), par)
+    monkeypatch.setenv("AIRG_SPGEMM_NO_ESC", "1")
+    Hb = airg.Hierarchy(*dev(p), par)
+    assert He.num_levels == Hb.num_levels
+    for l in range(He.num_levels):
+        names = ["A", "Ainv"] if He.level_info(l)["coarsest"] else ["A", "Ainv", "Z"]
+        for which in names:
+            for a, b in zip(He.export(l, which), Hb.export(l, which)):
+                assert np.array_equal(a, b), (l, which)
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_mixed_precision_sliced_ell_and_csr_agree_bitwise(monkeypatch, prec):
     # the float / bf16-value V-cycle reads the large residual operators from their sliced ELL copy
