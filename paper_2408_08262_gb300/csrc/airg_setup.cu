@@ -1314,7 +1314,7 @@ __device__ __forceinline__ int spg_rank_write(const SpgArgs& g, int* key, const 
 template <int CAP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int* __restrict__ rows,
                                                             const int* __restrict__ nrows_dev, int* next_rows,
-                                                            int* n_next) {
+                                                            int* n_next, int lim) {
   __shared__ int hkey[WARPS][CAP];
   __shared__ double hval[WARPS][CAP];
   const int nrows = *nrows_dev;
@@ -1326,7 +1326,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
   for (long long ii = gw; ii < nrows; ii += nw) {
     const int i = rows[ii];
     const long long ub = g.ubo[i + 1] - g.ubo[i];
-    if (ub > CAP) {
+    if (ub > lim) {
       if (lane == 0) next_rows[atomicAdd(n_next, 1)] = i;
       continue;
     }
@@ -1674,7 +1674,7 @@ __device__ __forceinline__ int esc_block_scan(int v, int* wsum, int* total) {
   return before + inc - v;
 }
 
-// Long rows (kWarpCap < candidates <= kEscCap, two tiers: 2048 and 4096): one 256-thread CTA per row, expand - sort -
+// Long rows (2048 < candidates <= kEscCap): one 256-thread CTA per row, expand - sort -
 // compress.  Every candidate (column j, A entry e, B value) gets a slot in the order A entries
 // ascending, each B row ascending; the 64-bit keys j << 32 | slot are sorted (bitonic, in shared
 // memory), so each column's candidates sit together in arrival order, and one thread folds each
@@ -1894,20 +1894,24 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
       stage_set = true;
     }
     airg::note_launch(), k_spgemm_warp_staged<<<152 * 3, kStageWarps * 32, stage_smem, s>>>(g, mid, ctr + 0, big, ctr + 1);
-    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2);
+    // rows above the hash kernel's limit go on to expand-sort (AIRG_SPGEMM_WARP_MAX lowers the limit)
+    int warp_lim = kWarpCap;
+    if (const char* wl = getenv("AIRG_SPGEMM_WARP_MAX")) warp_lim = std::max(32, std::min(kWarpCap, atoi(wl)));
+    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2, warp_lim);
     static bool esc_set = false;
     if (!esc_set) {
-      CU_TRY(cudaFuncSetAttribute(k_spgemm_esc<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esc_smem<2048>()));
       CU_TRY(cudaFuncSetAttribute(k_spgemm_esc<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esc_smem<4096>()));
       esc_set = true;
     }
-    // AIRG_SPGEMM_NO_ESC=1 sends every long row to the per-column block kernel (same results)
+    // rows of 1025-2048 candidates: the hash warp kernel with a 2048-slot table (two warps per
+    // CTA); 2049-4096: expand-sort-compress; beyond: the per-column block kernel.
+    // AIRG_SPGEMM_NO_ESC=1 sends every row above 1024 candidates to the block kernel (same results)
     const char* no_esc_env = getenv("AIRG_SPGEMM_NO_ESC");
     const bool no_esc = no_esc_env && no_esc_env[0] == '1';
     const int* blk_rows = lng;
     const int* blk_n = ctr + 2;
     if (!no_esc) {
-      airg::note_launch(), k_spgemm_esc<2048><<<152 * 3, 256, esc_smem<2048>(), s>>>(g, lng, ctr + 2, rest2, ctr + 7);
+      airg::note_launch(), k_spgemm_warp<2048, 2><<<152 * 4, 2 * 32, 0, s>>>(g, lng, ctr + 2, rest2, ctr + 7, 2048);
       airg::note_launch(), k_spgemm_esc<4096><<<152, 256, esc_smem<4096>(), s>>>(g, rest2, ctr + 7, rest, ctr + 6);
       blk_rows = rest;
       blk_n = ctr + 6;
