@@ -129,6 +129,23 @@ void airg_params_default(airg_params* p);
  * AIRG_ERR_ZERO_DIAG, AIRG_ERR_OOM, AIRG_ERR_CUDA, AIRG_ERR_UNSUPPORTED; *out is NULL then. */
 int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out);
 
+/* The same as airg_setup with A's three arrays in HOST memory (pinned memory lets the copies run
+ * at full speed; pageable memory works too): the library copies them to the device on `stream`
+ * inside the call and does not keep the host pointers.  With airg_solve_host, a caller whose data
+ * lives on the host sets up and solves through the C ABI alone. */
+int airg_setup_host(const airg_csr* A_host, const airg_params* p, airg_stream_t stream, airg_hierarchy** out);
+
+/* Setups of many independent systems (the batched form), run concurrently: `nthreads` host
+ * threads (<= 0: 8), each with a stream of its own, take the systems in turn and build their
+ * hierarchies as airg_setup does (same parameters for all; As: nsys device CSR descriptors).
+ * Small systems leave most of the GPU idle, and each setup waits on the host for its sizes, so
+ * running several at once fills the GPU.  Each hierarchy is bitwise the one airg_setup builds.
+ * Synchronises `stream` first (the inputs may be produced on it); returns once every hierarchy is
+ * built, each then belonging to `stream`.  outs: host array of nsys handles, each freed with
+ * airg_free.  On any error every handle is freed, set to NULL, and the first error returned. */
+int airg_setup_many(const airg_csr* As, int nsys, const airg_params* p, int nthreads, airg_stream_t stream,
+                    airg_hierarchy** outs);
+
 /* Setup re-use (Sections "Strong tolerances" and "Conclusions" name re-using the CF splitting
  * across the many solves of a Boltzmann problem).  Builds the hierarchy of A as airg_setup does,
  * except that the CF splittings of the first `levels` levels (levels <= 0: every non-coarsest level

@@ -61,6 +61,9 @@ def lib():
             raise ImportError(f"libairg.so not built ({LIB_PATH}); run paper_2408_08262_gb300.build.build()")
         L = C.CDLL(LIB_PATH)
         L.airg_setup.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_setup_host.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.airg_setup_many.argtypes = [C.POINTER(_Csr), C.c_int, C.POINTER(_Params), C.c_int, C.c_void_p,
+                                      C.POINTER(C.c_void_p)]
         L.airg_setup_reuse.argtypes = [C.POINTER(_Csr), C.POINTER(_Params), C.c_void_p, C.c_int, C.c_void_p,
                                        C.POINTER(C.c_void_p)]
         L.airg_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_Opts), C.POINTER(_Info), C.c_void_p]
@@ -95,7 +98,7 @@ def lib():
     return _lib
 
 
-EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_reuse", "airg_setup_transpose", "airg_ddc_theta", "airg_transpose", "airg_sddmm",
+EXPORTED = ["airg_params_default", "airg_setup", "airg_setup_host", "airg_setup_many", "airg_setup_reuse", "airg_setup_transpose", "airg_ddc_theta", "airg_transpose", "airg_sddmm",
             "airg_solve", "airg_solve_host", "airg_vcycle", "airg_cf_split", "airg_batch_create",
             "airg_solve_batched", "airg_batch_free", "airg_batch_tuned",
             "airg_cf_split_noalloc",
@@ -145,11 +148,12 @@ def _check(code: int, what: str, allow_not_converged: bool = False):
     raise AirgError(code, what)
 
 
-def _csr(rowptr, col, val) -> _Csr:
+def _csr(rowptr, col, val, host: bool = False) -> _Csr:
     import torch
     for t, dt in ((rowptr, torch.int32), (col, torch.int32), (val, torch.float64)):
-        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
-            raise TypeError("CSR arrays must be contiguous CUDA tensors (int32, int32, float64)")
+        if not (t.is_cuda != host and t.dtype == dt and t.is_contiguous()):
+            where = "CPU" if host else "CUDA"
+            raise TypeError(f"CSR arrays must be contiguous {where} tensors (int32, int32, float64)")
     return _Csr(rowptr.numel() - 1, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
 
 
@@ -157,16 +161,22 @@ class Hierarchy:
     """An AIRG hierarchy built on the GPU (airg_setup)."""
 
     def __init__(self, rowptr, col, val, params: Params | None = None, stream=None, transpose: bool = False,
-                 reuse: "Hierarchy | None" = None, reuse_levels: int = 0):
+                 reuse: "Hierarchy | None" = None, reuse_levels: int = 0, host: bool = False):
         """transpose=True builds the hierarchy of A^T (airg_setup_transpose), for adjoint solves.
         reuse=T takes the CF splittings of T's first reuse_levels levels (0: all) instead of computing
-        them (airg_setup_reuse); the matrix should share T's sparsity pattern."""
+        them (airg_setup_reuse); the matrix should share T's sparsity pattern.  host=True takes CPU
+        tensors (pinned ones copy fastest) and lets the library copy them in (airg_setup_host)."""
         self.params = params or Params()
         self._keep = (rowptr, col, val)
-        A = _csr(rowptr, col, val)
+        A = _csr(rowptr, col, val, host=host)
         self.n = A.n
         h = C.c_void_p()
-        if reuse is not None:
+        if host:
+            if transpose or reuse is not None:
+                raise TypeError("host=True builds a plain hierarchy (no transpose or re-use)")
+            _check(lib().airg_setup_host(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)),
+                   "airg_setup_host")
+        elif reuse is not None:
             _check(lib().airg_setup_reuse(C.byref(A), C.byref(self.params.c()), reuse._h, reuse_levels,
                                           _stream(stream), C.byref(h)), "airg_setup_reuse")
         else:
@@ -174,6 +184,13 @@ class Hierarchy:
             _check(fn(C.byref(A), C.byref(self.params.c()), _stream(stream), C.byref(h)),
                    "airg_setup_transpose" if transpose else "airg_setup")
         self._h = h
+
+    @classmethod
+    def _adopt(cls, handle, n, params, keep):
+        """A Hierarchy object around a handle the library built (airg_setup_many)."""
+        H = cls.__new__(cls)
+        H.params, H._keep, H.n, H._h = params, keep, n, handle
+        return H
 
     def close(self):
         if getattr(self, "_h", None):
@@ -302,6 +319,16 @@ class Hierarchy:
         _check(lib().airg_kernel_times_level(self._h, level, la.ctypes.data, ms.ctypes.data, by.ctypes.data, n),
                "airg_kernel_times_level")
         return {c: dict(launches=int(la[i]), ms=float(ms[i]), bytes=float(by[i])) for i, c in enumerate(PROFILE_CLASSES)}
+
+
+def setup_many(mats, params: Params | None = None, nthreads: int = 8, stream=None) -> list:
+    """Hierarchies of many independent systems built concurrently (airg_setup_many): mats is a list
+    of (rowptr, col, val) CUDA tensor triples; returns one Hierarchy per system."""
+    p = params or Params()
+    arr = (_Csr * len(mats))(*[_csr(*m) for m in mats])
+    hs = (C.c_void_p * len(mats))()
+    _check(lib().airg_setup_many(arr, len(mats), C.byref(p.c()), nthreads, _stream(stream), hs), "airg_setup_many")
+    return [Hierarchy._adopt(C.c_void_p(h), m[0].numel() - 1, p, m) for h, m in zip(hs, mats)]
 
 
 def cf_split(rowptr, col, val, params: Params | None = None, level: int = 0, stream=None):

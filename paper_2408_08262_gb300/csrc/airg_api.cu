@@ -5,6 +5,10 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
+#include <vector>
+#include <atomic>
+#include <thread>
 #include <new>
 
 #include "airg_hier.cuh"
@@ -85,7 +89,7 @@ static int keep_polynomial(const LevelBuild& L, SolveLevel& S, Arena& a, cudaStr
   return AIRG_OK;
 }
 
-int setup_impl(airg_hierarchy* H, const airg_csr* Ain, const airg_hierarchy* T, int reuse_levels) {
+int setup_impl(airg_hierarchy* H, const airg_csr* Ain, const airg_hierarchy* T, int reuse_levels, bool host_input) {
   cudaStream_t s = H->s;
   SetupParams sp = to_setup(H->p);
   if (sp.coarse_size <= 0) sp.coarse_size = (int)std::min<long long>(60000, std::max<long long>(64, (long long)Ain->n / 16));
@@ -102,9 +106,10 @@ int setup_impl(airg_hierarchy* H, const airg_csr* Ain, const airg_hierarchy* T, 
   } rel{tmp};
   DCsr A0;
   AIRG_TRY(H->setup_mem.csr(A0, Ain->n, Ain->n, Ain->nnz));
-  CU_TRY(cudaMemcpyAsync(A0.rp, Ain->rowptr, sizeof(int) * ((size_t)Ain->n + 1), cudaMemcpyDeviceToDevice, s));
-  CU_TRY(cudaMemcpyAsync(A0.ci, Ain->col, sizeof(int) * (size_t)Ain->nnz, cudaMemcpyDeviceToDevice, s));
-  CU_TRY(cudaMemcpyAsync(A0.v, Ain->val, sizeof(double) * (size_t)Ain->nnz, cudaMemcpyDeviceToDevice, s));
+  const cudaMemcpyKind kind = host_input ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CU_TRY(cudaMemcpyAsync(A0.rp, Ain->rowptr, sizeof(int) * ((size_t)Ain->n + 1), kind, s));
+  CU_TRY(cudaMemcpyAsync(A0.ci, Ain->col, sizeof(int) * (size_t)Ain->nnz, kind, s));
+  CU_TRY(cudaMemcpyAsync(A0.v, Ain->val, sizeof(double) * (size_t)Ain->nnz, kind, s));
   AIRG_TRY(validate_csr(A0, tmp, s));
   H->n0 = Ain->n;
   H->top_nnz = Ain->nnz;
@@ -376,7 +381,7 @@ void airg_params_default(airg_params* p) {
 }
 
 static int setup_common(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out,
-                        const airg_hierarchy* T, int reuse_levels) {
+                        const airg_hierarchy* T, int reuse_levels, bool host_input = false) {
   if (!out) return AIRG_ERR_ARG;
   *out = nullptr;
   AIRG_TRY(check_csr_arg(A));
@@ -404,7 +409,7 @@ static int setup_common(const airg_csr* A, const airg_params* p, airg_stream_t s
     cudaGetLastError();
   }
   auto t0 = std::chrono::steady_clock::now();
-  int rc = setup_impl(H, A, T, reuse_levels);
+  int rc = setup_impl(H, A, T, reuse_levels, host_input);
   if (rc != AIRG_OK) {
     cudaGetLastError();
     destroy(H);
@@ -417,6 +422,63 @@ static int setup_common(const airg_csr* A, const airg_params* p, airg_stream_t s
 
 int airg_setup(const airg_csr* A, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
   return setup_common(A, p, stream, out, nullptr, 0);
+}
+
+int airg_setup_host(const airg_csr* A_host, const airg_params* p, airg_stream_t stream, airg_hierarchy** out) {
+  return setup_common(A_host, p, stream, out, nullptr, 0, true);
+}
+
+int airg_setup_many(const airg_csr* As, int nsys, const airg_params* p, int nthreads, airg_stream_t stream,
+                    airg_hierarchy** outs) {
+  if (!As || !outs || nsys <= 0) return AIRG_ERR_ARG;
+  for (int q = 0; q < nsys; ++q) outs[q] = nullptr;
+  AIRG_TRY(check_params(p));
+  for (int q = 0; q < nsys; ++q) AIRG_TRY(check_csr_arg(&As[q]));
+  int dev = 0;
+  CU_TRY(cudaGetDevice(&dev));
+  // the inputs may still be being written on the caller's stream
+  CU_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  const int nt = std::max(1, std::min(nthreads <= 0 ? 8 : nthreads, nsys));
+  std::atomic<int> next{0};
+  std::vector<int> rcs(nsys, AIRG_OK);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t ws = nullptr;
+    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (int q; (q = next.fetch_add(1)) < nsys;) rcs[q] = AIRG_ERR_CUDA;
+      return;
+    }
+    for (int q; (q = next.fetch_add(1)) < nsys;) {
+      rcs[q] = setup_common(&As[q], p, (airg_stream_t)ws, &outs[q], nullptr, 0);
+      if (rcs[q] == AIRG_OK && cudaStreamSynchronize(ws) != cudaSuccess) rcs[q] = AIRG_ERR_CUDA;
+    }
+    cudaStreamSynchronize(ws);
+    cudaStreamDestroy(ws);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  int rc = AIRG_OK;
+  for (int q = 0; q < nsys; ++q)
+    if (rcs[q] != AIRG_OK && rc == AIRG_OK) rc = rcs[q];
+  if (rc != AIRG_OK) {
+    for (int q = 0; q < nsys; ++q) {
+      if (outs[q]) outs[q]->s = (cudaStream_t)stream;
+      airg_free(outs[q]);
+      outs[q] = nullptr;
+    }
+    return rc;
+  }
+  // every hierarchy now belongs to the caller's stream (the worker streams are gone)
+  for (int q = 0; q < nsys; ++q) {
+    airg_hierarchy* H = outs[q];
+    H->s = (cudaStream_t)stream;
+    H->solve_mem.s = H->s;
+    H->setup_mem.s = H->s;
+  }
+  return AIRG_OK;
 }
 
 int airg_setup_reuse(const airg_csr* A, const airg_params* p, const airg_hierarchy* T, int levels,

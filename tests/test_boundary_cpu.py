@@ -115,3 +115,18 @@ def test_parameter_and_argument_checks_run_before_any_device_work(libpath):
     # beyond the fixed array: rejected with its own code, still before any device work
     Abig = airg._Csr(10_000_000, 100_000_000, 16, 32, 48)
     assert L.airg_cf_split_noalloc(ctypes.byref(Abig), ctypes.byref(p), 0, cfo, None) == -8
+
+
+def test_host_setup_checks_its_arguments_before_any_device_work(libpath):
+    # airg_setup_host takes airg_setup's argument and parameter checks (host-side)
+    from paper_2408_08262_gb300 import airg
+    L = airg.lib()
+    out = ctypes.c_void_p()
+    p = airg.Params().c()
+    assert L.airg_setup_host(None, ctypes.byref(p), None, ctypes.byref(out)) == -1
+    A = airg._Csr(8, 8, 16, 32, 48)
+    assert L.airg_setup_host(ctypes.byref(A), None, None, ctypes.byref(out)) == -1
+    bad = airg.Params(poly_order=15).c()
+    assert L.airg_setup_host(ctypes.byref(A), ctypes.byref(bad), None, ctypes.byref(out)) == -1
+    assert L.airg_setup_host(ctypes.byref(A), ctypes.byref(p), None, None) == -1
+    assert out.value is None

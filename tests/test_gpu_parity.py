@@ -392,6 +392,23 @@ def test_setup_reuse_with_strength_zero_is_a_fresh_setup():
     assert torch.equal(xf, xr)
 
 
+def test_host_buffer_setup_and_solve_equal_the_device_ones():
+    # airg_setup_host copies the CSR arrays in itself; with airg_solve_host a caller with host data
+    # goes through the C ABI alone, and the solution is bitwise the device path's
+    p = P.blocked_sigma_2d(96)
+    host = [torch.from_numpy(a).pin_memory() for a in (p.rowptr, p.col, p.val)]
+    Hh = airg.Hierarchy(*host, airg.Params(), host=True)
+    Hd = airg.Hierarchy(*dev(p), airg.Params())
+    bh = torch.from_numpy(p.b).pin_memory()
+    xh = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    _, ih = Hh.solve_host(bh, xh, rtol=1e-10)
+    xd, i_d = Hd.solve(torch.from_numpy(p.b).cuda(), rtol=1e-10)
+    assert ih["status"] == 0 and ih["iters"] == i_d["iters"]
+    assert torch.equal(xh, xd.cpu())
+    with pytest.raises(TypeError):
+        airg.Hierarchy(*dev(p), airg.Params(), host=True)
+
+
 def test_setup_reuse_across_directions():
     # directions of one mesh that share the upwind pattern (unjittered cells, angles inside one
     # 45-degree sector): with strength 0 the re-used level-0 splitting of another direction is the
