@@ -274,12 +274,24 @@ def batched_form(args, airg, P, torch, dev, stream, params, dist, world: int, ra
     systems = [systems_all[i] for i in mine]
     infos, its_seq, tuned = [], [], []
     tb = ts = tr = 0.0
-    tsu = tcr = 0.0
+    tsu = tcr = tsm = 0.0
     if systems:
         mats = [tuple(torch.from_numpy(a).to(dev) for a in (q.rowptr, q.col, q.val)) for q in systems]
         bs = [torch.from_numpy(q.b).to(dev) for q in systems]
         for m in mats[:2]:  # warm-up of the setup path
             airg.Hierarchy(*m, params).close()
+        for H in airg.setup_many(mats[:8], params):
+            H.close()
+        # the batched form's setups: all systems concurrently (airg_setup_many)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Hm = airg.setup_many(mats, params)
+        torch.cuda.synchronize(dev)
+        tsm = 1e3 * (time.perf_counter() - t0)
+        for H in Hm:
+            H.close()
+        del Hm
+        # the same setups one after another (the plain form)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         Hs = [airg.Hierarchy(*m, params) for m in mats]
@@ -324,6 +336,7 @@ def batched_form(args, airg, P, torch, dev, stream, params, dist, world: int, ra
     ts = max_over_ranks(ts, dist, dev)
     tsu = max_over_ranks(tsu, dist, dev)
     tcr = max_over_ranks(tcr, dist, dev)
+    tsm = max_over_ranks(tsm, dist, dev)
     tr = max_over_ranks(tr, dist, dev)
     ndofs = int(sum_over_ranks(sum(q.n for q in systems), dist, dev))
     nsys = int(sum_over_ranks(len(systems), dist, dev))
@@ -336,9 +349,10 @@ def batched_form(args, airg, P, torch, dev, stream, params, dist, world: int, ra
                "systems_per_rank_max": int(max_over_ranks(len(systems), dist, dev)),
                "batched_solve_ms": round(tb, 2), "sequential_solve_ms": round(ts, 2),
                "speedup_vs_sequential": round(ts / tb, 3), "batched_dofs_per_s": ndofs / (tb / 1e3),
-               "setups_ms": round(tsu, 2), "batch_create_and_autotune_ms": round(tcr, 2),
-               "time_to_rtol_batched_ms": round(tsu + tcr + tb, 2), "time_to_rtol_sequential_ms": round(tsu + ts, 2),
-               "time_to_rtol_speedup_vs_sequential": round((tsu + ts) / max(tsu + tcr + tb, 1e-9), 3),
+               "setups_concurrent_ms": round(tsm, 2), "setups_sequential_ms": round(tsu, 2),
+               "batch_create_and_autotune_ms": round(tcr, 2),
+               "time_to_rtol_batched_ms": round(tsm + tcr + tb, 2), "time_to_rtol_sequential_ms": round(tsu + ts, 2),
+               "time_to_rtol_speedup_vs_sequential": round((tsu + ts) / max(tsm + tcr + tb, 1e-9), 3),
                "iters_min": int(it_min), "iters_max": int(it_max), "all_converged": failed == 0.0,
                "iters_sequential_max": int(it_seq)}
     batched["autotuner"] = {"groups_tuned": len(tuned), "changed_from_rule": sum(r != c for r, c in tuned),
@@ -527,16 +541,16 @@ def main():
     t_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     value = job_value(p.n, args.steps, world, t_ms / 1e3)
 
-    # end to end through the public API with host buffers: matrix and rhs copied in from pinned
-    # host memory, solution copied back, inside the timed region
+    # end to end through the public API with host buffers: the library copies the matrix
+    # (airg_setup_host) and the rhs (airg_solve_host) in from pinned host memory and the solution
+    # back, inside the timed region
     x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
     h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 8 + b_h.numel() * 8
     d2h = x_h.numel() * 8
     torch.cuda.synchronize(dev)
     e0 = time.perf_counter()
     for _ in range(args.steps):
-        rp2, ci2, v2 = (t.to(dev, non_blocking=True) for t in (rp_h, ci_h, v_h))
-        H = airg.Hierarchy(rp2, ci2, v2, params)
+        H = airg.Hierarchy(rp_h, ci_h, v_h, params, host=True)
         H.solve_host(b_h, x_h, rtol=args.rtol, restart=args.restart)
         H.close()
     torch.cuda.synchronize(dev)

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "airg_common.cuh"
@@ -1850,6 +1851,25 @@ __global__ void k_i64_to_i32(int n, const long long* __restrict__ in, int* __res
 
 // Product into the padded form: row i's cnt[i] entries at tcol/tval + ubo[i] (ubo = exclusive scan
 // of the candidate counts).  B is CSR (Bc) or padded (Bp).
+// Dynamic shared-memory limits of the product kernels, set once per process (setups may run
+// concurrently on several host threads).
+static int spgemm_smem_attributes() {
+  static std::once_flag once;
+  static int rc = AIRG_OK;
+  std::call_once(once, [] {
+    int r = cuda_status(cudaFuncSetAttribute(k_spgemm_warp_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(WarpStage) * kStageWarps)));
+    if (r == AIRG_OK)
+      r = cuda_status(cudaFuncSetAttribute(k_spgemm_esc<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)esc_smem<4096>()));
+    if (r == AIRG_OK)
+      r = cuda_status(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(int) * (size_t)kBlockCapMax)));
+    rc = r;
+  });
+  return rc;
+}
+
 int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double scale, double tol, bool keep_diag,
                   SpgPadded& out, Arena& tmp, cudaStream_t s) {
   const int ar = A.nrows;
@@ -1887,22 +1907,10 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
   CU_TRY(cudaMemsetAsync(ctr, 0, 8 * sizeof(int), s));
   if (ar > 0) {
     airg::note_launch(), k_spgemm_thread<<<grid_for(ar, 128, 152 * 64), 128, 0, s>>>(g, mid, ctr + 0);
-    static bool stage_set = false;
+    AIRG_TRY(spgemm_smem_attributes());
     const size_t stage_smem = sizeof(WarpStage) * kStageWarps;
-    if (!stage_set) {
-      CU_TRY(cudaFuncSetAttribute(k_spgemm_warp_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem));
-      stage_set = true;
-    }
     airg::note_launch(), k_spgemm_warp_staged<<<152 * 3, kStageWarps * 32, stage_smem, s>>>(g, mid, ctr + 0, big, ctr + 1);
-    // rows above the hash kernel's limit go on to expand-sort (AIRG_SPGEMM_WARP_MAX lowers the limit)
-    int warp_lim = kWarpCap;
-    if (const char* wl = getenv("AIRG_SPGEMM_WARP_MAX")) warp_lim = std::max(32, std::min(kWarpCap, atoi(wl)));
-    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2, warp_lim);
-    static bool esc_set = false;
-    if (!esc_set) {
-      CU_TRY(cudaFuncSetAttribute(k_spgemm_esc<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esc_smem<4096>()));
-      esc_set = true;
-    }
+    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2, kWarpCap);
     // rows of 1025-2048 candidates: the hash warp kernel with a 2048-slot table (two warps per
     // CTA); 2049-4096: expand-sort-compress; beyond: the per-column block kernel.
     // AIRG_SPGEMM_NO_ESC=1 sends every row above 1024 candidates to the block kernel (same results)
@@ -1916,12 +1924,7 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
       blk_rows = rest;
       blk_n = ctr + 6;
     }
-    static bool smem_set = false;
     const size_t smem = sizeof(int) * (size_t)kBlockCapMax;
-    if (!smem_set) {
-      CU_TRY(cudaFuncSetAttribute(k_spgemm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      smem_set = true;
-    }
     airg::note_launch(), k_spgemm_block<<<152, 256, smem, s>>>(g, blk_rows, blk_n, kBlockCapMax, ctr + 3);
     KERNEL_CHECK();
   }

@@ -130,3 +130,18 @@ def test_host_setup_checks_its_arguments_before_any_device_work(libpath):
     assert L.airg_setup_host(ctypes.byref(A), ctypes.byref(bad), None, ctypes.byref(out)) == -1
     assert L.airg_setup_host(ctypes.byref(A), ctypes.byref(p), None, None) == -1
     assert out.value is None
+
+
+def test_concurrent_setups_check_their_arguments_before_any_device_work(libpath):
+    from paper_2408_08262_gb300 import airg
+    L = airg.lib()
+    p = airg.Params().c()
+    outs = (ctypes.c_void_p * 2)()
+    As = (airg._Csr * 2)(airg._Csr(8, 8, 16, 32, 48), airg._Csr(8, 8, None, 32, 48))
+    assert L.airg_setup_many(None, 2, ctypes.byref(p), 2, None, outs) == -1
+    assert L.airg_setup_many(As, 0, ctypes.byref(p), 2, None, outs) == -1
+    assert L.airg_setup_many(As, 2, ctypes.byref(p), 2, None, outs) == -1  # second CSR has no row pointers
+    bad = airg.Params(coarse_iters=0).c()
+    assert L.airg_setup_many(As, 1, ctypes.byref(bad), 2, None, outs) == -1
+    assert L.airg_setup_many(As, 1, ctypes.byref(p), 2, None, None) == -1
+    assert outs[0] is None and outs[1] is None

@@ -103,3 +103,31 @@ def test_batched_at_the_full_system_sizes():
     assert io["status"] == 0
     assert np.linalg.norm(xs[1].cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-10
     B.close()
+
+
+def test_concurrent_setups_equal_the_individual_setups():
+    # airg_setup_many builds the hierarchies of many systems on several host threads and streams at
+    # once; every hierarchy must be bitwise the one airg_setup builds, and they batch as usual
+    ps = systems() + [P.p1_dg_2d(128, 0.7, sigma=2.0, seed=1010), P.p1_dg_2d(96, 5.1, sigma=0.0, seed=1011)]
+    par = airg.Params(coarse_size=64, keep_setup=1)
+    mats = [dev(p) for p in ps]
+    Hm = airg.setup_many(mats, par, nthreads=4)
+    Hs = [airg.Hierarchy(*m, par) for m in mats]
+    for Ha, Hb in zip(Hm, Hs):
+        assert Ha.num_levels == Hb.num_levels
+        for l in range(Ha.num_levels):
+            names = ["A", "Ainv"] if Ha.level_info(l)["coarsest"] else ["A", "Ainv", "Z", "AF_solve", "Z_solve"]
+            for which in names:
+                for a, b in zip(Ha.export(l, which), Hb.export(l, which)):
+                    assert np.array_equal(a, b), (l, which)
+    bs = [torch.from_numpy(p.b).cuda() for p in ps]
+    for Ha, Hb, b in zip(Hm, Hs, bs):
+        xa, ia = Ha.solve(b, rtol=1e-12)
+        xb, ib = Hb.solve(b, rtol=1e-12)
+        assert ia == ib and torch.equal(xa, xb)
+    B = airg.Batch(Hm)
+    xs, infos = B.solve(bs, rtol=1e-12)
+    assert all(i["status"] == 0 for i in infos)
+    B.close()
+    for H in Hm + Hs:
+        H.close()
