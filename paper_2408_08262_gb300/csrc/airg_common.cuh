@@ -5,6 +5,7 @@
 //     unknowns F-points first and its C-points (= level l+1's unknowns, in level l+1's own F-then-C
 //     order) last.  Restriction, recursion and prolongation therefore never permute.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -182,6 +183,43 @@ void dev_add(const double* y, double* x, int n, cudaStream_t s);
 int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double* coef, double* y, int lanes,
                   cudaStream_t s);
 int pick_lanes(double avg_row_len);
+// Solve operators whose arrays take at most this many MiB are read with the evict-normal L2
+// policy (AIRG_L2_KEEP_MB overrides; l2_keep_bytes gives the size in bytes), larger ones with
+// evict-first.
+constexpr int kL2KeepMB = 64;
+double l2_keep_bytes();
+#ifdef __CUDACC__
+// Loads of an operator's columns and values with an L2 eviction policy held in a register:
+// evict-first for operators that stream through L2 once per use (they would only displace the
+// vectors), evict-normal for operators small enough that the level's second smoothing pass and
+// the coarsest level's iterations find them still in L2.
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+  uint64_t p;
+  if (keep) asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int ld_pol(const int* p, uint64_t pol) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_pol(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_pol(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ __nv_bfloat16 ld_pol(const __nv_bfloat16* p, uint64_t pol) {
+  unsigned short v;
+  asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return __ushort_as_bfloat16(v);
+}
+#endif
 // r = b_F - AF x with x_F taken as the one-point prolongation of x_C (x[f] = x[nf + w[f]]), which
 // is also stored into x_F.  AF has nf rows; x holds [x_F, x_C].
 int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double* b, double* y, int lanes,

@@ -3,6 +3,8 @@
 // cores (nothing here is a dense contraction).
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+
 #include "airg_common.cuh"
 
 namespace airg {
@@ -324,8 +326,8 @@ int dev_multi_axpy(const double* V, long long ldv, int ncols, const double* y, d
 }
 
 // ------------------------------------------------------------------------------------------
-// CSR SpMV.  Every kernel reads the rows' entries directly (columns and values streamed with
-// evict-first loads, so that x stays in L2), gathers x and accumulates with one fused multiply-add
+// CSR SpMV.  Every kernel reads the rows' entries directly (columns and values with an L2 policy
+// chosen per operator, see l2_policy), gathers x and accumulates with one fused multiply-add
 // per entry: one thread per row for short rows (k_spmv_row), LPR lanes per row for longer ones
 // (k_spmv_vec).  PROLONG: first F-smoothing residual with the one-point prolongation fused in (see
 // dev_spmv_resid_prolong).  VT is the stored value type (double, float or bf16), XT the vector and
@@ -346,20 +348,22 @@ __device__ __forceinline__ float vfma<__nv_bfloat16, float>(__nv_bfloat16 a, flo
 
 
 
-// Entries k0 .. k0+R-1 of a row (those below re): loads, then gathers of x, then R FMAs in
-// entry order.  R is a compile-time count, so that the FP64 FMAs a warp issues stop at its longest
-// row: on sm_103a the FP64 pipe takes about 64 cycles per warp instruction whether or not its
-// lanes are predicated off, and the SpMVs are close to that pipe's rate.
-template <typename VT, typename XT, bool PROLONG, int R>
+// Entries k0, k0 + STRIDE, ..., k0 + (R-1) STRIDE of a row (those below re): loads, then gathers
+// of x, then R FMAs in entry order.  R is a compile-time count, so that the FP64 FMAs a warp issues
+// stop at its longest row (or lane share): on sm_103a the FP64 pipe takes about 64 cycles per warp
+// instruction whether or not its lanes are predicated off, and the SpMVs are close to that pipe's
+// rate.
+template <typename VT, typename XT, bool PROLONG, int R, int STRIDE = 1>
 __device__ __forceinline__ XT row_entries(const int* __restrict__ ci, const VT* __restrict__ v, int k0, int re,
-                                          const XT* x, int nrows, const int* __restrict__ w, XT s) {
-  int c[R];
+                                          const XT* x, int nrows, const int* __restrict__ w, XT s, uint64_t pol) {
   VT a[R];
   XT xv[R];
+  int c[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    c[t] = (k0 + t < re) ? __ldcs(ci + k0 + t) : -1;
-    a[t] = (k0 + t < re) ? __ldcs(v + k0 + t) : VT(0);
+    const int k = k0 + t * STRIDE;
+    c[t] = (k < re) ? ld_pol(ci + k, pol) : -1;
+    a[t] = (k < re) ? ld_pol(v + k, pol) : VT(0);
   }
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -379,158 +383,185 @@ __device__ __forceinline__ XT row_entries(const int* __restrict__ ci, const VT* 
   return s;
 }
 
+// The last r (< RB) entries of a row or lane share, with an exact compile-time count.
+template <typename VT, typename XT, bool PROLONG, int RB, int STRIDE>
+__device__ __forceinline__ XT entries_tail(int r, const int* __restrict__ ci, const VT* __restrict__ v, int k0, int re,
+                                           const XT* x, int nrows, const int* __restrict__ w, XT s, uint64_t pol) {
+  switch (r) {
+    case 1: return row_entries<VT, XT, PROLONG, 1, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+    case 2: return row_entries<VT, XT, PROLONG, 2, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+    case 3: return row_entries<VT, XT, PROLONG, 3, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+    default: break;
+  }
+  if constexpr (RB > 4) {
+    switch (r) {
+      case 4: return row_entries<VT, XT, PROLONG, 4, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+      case 5: return row_entries<VT, XT, PROLONG, 5, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+      case 6: return row_entries<VT, XT, PROLONG, 6, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+      case 7: return row_entries<VT, XT, PROLONG, 7, STRIDE>(ci, v, k0, re, x, nrows, w, s, pol);
+      default: break;
+    }
+  }
+  return s;
+}
+
+// The row's own operand of the output (b, or y for the accumulating mode), loaded before the
+// entries so that its round trip overlaps theirs instead of following the sum.
+template <int MODE, typename XT>
+__device__ __forceinline__ XT row_operand(const XT* b, const XT* y, int row) {
+  if (MODE == SPMV_SET) return XT(0);
+  if (MODE == SPMV_ADD) return y[row];
+  return b[row];
+}
+template <int MODE, typename XT>
+__device__ __forceinline__ XT row_output(XT pre, XT s, const XT* __restrict__ coef) {
+  if (MODE == SPMV_SET) return s;
+  if (MODE == SPMV_RESID) return pre - s;
+  if (MODE == SPMV_AXPB) return coef[0] * pre + s;
+  return pre + s;  // SPMV_ADD, SPMV_ADDB
+}
+// One-point prolongation of the row's own F-point (PROLONG): its C source's value, or 0.
+template <typename XT>
+__device__ __forceinline__ XT row_prolong(const XT* x, int nrows, const int* __restrict__ w, int row) {
+  const int src = w[row];
+  return src >= 0 ? x[nrows + src] : XT(0);
+}
+
 // Short rows (average <= 12 entries): one thread per row reads its own entries directly, kRowBatch
 // (4 for rows of about 4 entries or fewer, else 8) at a time (the warp's rows are contiguous, so
 // the lines they touch arrive once in L1), up to the warp's longest row, and accumulates with one
-// fused multiply-add per entry, in storage order; no shared memory and no barrier.
+// fused multiply-add per entry, in storage order; no shared memory and no barrier.  Resident CTAs
+// per SM the register budget allows: eight (32 registers) for the 4-entry batches, five (48) for
+// the 8-entry ones; the fused-prolongation variants are left unbounded.
+constexpr int kRowBlocks4 = 8, kRowBlocks8 = 5;
 template <typename VT, typename XT, int MODE, bool PROLONG, int kRowBatch>
-__global__ void __launch_bounds__(256, (kRowBatch == 4 && !PROLONG) ? 8 : 1) k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                  const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
-                                                  const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
-  for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < nrows; rr += (long long)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256, PROLONG ? 1 : (kRowBatch == 4 ? kRowBlocks4 : kRowBlocks8))
+    k_spmv_row(int nrows, const int* __restrict__ rp, const int* __restrict__ ci, const VT* __restrict__ v, const XT* x,
+               const XT* b, XT* y, const int* __restrict__ w, XT* xf, const XT* __restrict__ coef, bool keep) {
+  const uint64_t pol = l2_policy(keep);
+  // the grid holds one thread per row
+  const long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rr < nrows) {
     const int row = (int)rr;
+    const XT pre = row_operand<MODE>(b, y, row);
+    const XT pro = PROLONG ? row_prolong(x, nrows, w, row) : XT(0);
     const int rb = rp[row], re = rp[row + 1];
     const int wmax = (int)__reduce_max_sync(__activemask(), (unsigned)(re - rb));  // uniform over the lanes here
     XT s = XT(0);
     int j0 = 0;
     for (; j0 + kRowBatch <= wmax; j0 += kRowBatch)
-      s = row_entries<VT, XT, PROLONG, kRowBatch>(ci, v, rb + j0, re, x, nrows, w, s);
-    switch (wmax - j0) {
-      case 1: s = row_entries<VT, XT, PROLONG, 1>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 2: s = row_entries<VT, XT, PROLONG, 2>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 3: s = row_entries<VT, XT, PROLONG, 3>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 4: s = row_entries<VT, XT, PROLONG, 4>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 5: s = row_entries<VT, XT, PROLONG, 5>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 6: s = row_entries<VT, XT, PROLONG, 6>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      case 7: s = row_entries<VT, XT, PROLONG, 7>(ci, v, rb + j0, re, x, nrows, w, s); break;
-      default: break;
-    }
-    XT out;
-    if (MODE == SPMV_SET) out = s;
-    else if (MODE == SPMV_RESID) out = b[row] - s;
-    else if (MODE == SPMV_ADD) out = y[row] + s;
-    else if (MODE == SPMV_AXPB) out = coef[0] * b[row] + s;
-    else out = b[row] + s;
-    y[row] = out;
-    if (PROLONG) {
-      const int src = w[row];
-      xf[row] = src >= 0 ? x[nrows + src] : XT(0);
-    }
+      s = row_entries<VT, XT, PROLONG, kRowBatch>(ci, v, rb + j0, re, x, nrows, w, s, pol);
+    s = entries_tail<VT, XT, PROLONG, kRowBatch, 1>(wmax - j0, ci, v, rb + j0, re, x, nrows, w, s, pol);
+    y[row] = row_output<MODE>(pre, s, coef);
+    if (PROLONG) xf[row] = pro;
   }
 }
 
-// Longer rows (LPR = 2..32 lanes per row): the LPR lanes of a row read its entries directly,
-// lane l taking entries l, l + LPR, ... (4 per batch), accumulate with FMAs and combine by a
-// butterfly over the LPR lanes.  No shared memory and no barrier.
+// Longer rows (LPR = 2..32 lanes per row): the LPR lanes of a row read its entries directly, lane l
+// taking entries l, l + LPR, ..., 8 per batch up to the warp's largest lane share (so the warp
+// issues exactly that many FMAs and one round trip of loads per batch), accumulate with FMAs and
+// combine by a butterfly over the LPR lanes.  No shared memory and no barrier.  Five resident CTAs
+// per SM (48 registers); the fused-prolongation variant, whose gathers hold more registers, takes
+// 4-entry batches at six CTAs, so that the small levels' launches fit in one wave.
+constexpr int kVecBlocks = 5, kVecBlocksProlong = 6;
 template <typename VT, typename XT, int LPR, int MODE, bool PROLONG>
-__global__ void __launch_bounds__(256, PROLONG ? 6 : 8) k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                  const VT* __restrict__ v, const XT* x, const XT* b, XT* y,
-                                                  const int* __restrict__ w, XT* xf, const XT* __restrict__ coef) {
+__global__ void __launch_bounds__(256, PROLONG ? kVecBlocksProlong : kVecBlocks)
+    k_spmv_vec(int nrows, const int* __restrict__ rp, const int* __restrict__ ci, const VT* __restrict__ v, const XT* x,
+               const XT* b, XT* y, const int* __restrict__ w, XT* xf, const XT* __restrict__ coef, bool keep) {
   constexpr int GPW = 32 / LPR;  // rows per warp and pass
+  constexpr int kVecBatch = PROLONG ? 4 : 8;
+  const uint64_t pol = l2_policy(keep);
   const int lane = threadIdx.x % LPR, grp = (threadIdx.x & 31) / LPR;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  // warp-uniform loop, so that every lane reaches the butterfly below
-  for (long long base = warp * GPW; base < nrows; base += nwarps * GPW) {
+  // the grid holds one group of LPR lanes per row; the test below is warp-uniform, so that every
+  // lane reaches the butterfly
+  const long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW;
+  if (base < nrows) {
     const long long rr = base + grp;
     const bool act = rr < nrows;
     const int row = act ? (int)rr : 0;
+    const bool own = act && lane == 0;
+    const XT pre = own ? row_operand<MODE>(b, y, row) : XT(0);
+    const XT pro = (PROLONG && own) ? row_prolong(x, nrows, w, row) : XT(0);
     const int rb = act ? rp[row] : 0, re = act ? rp[row + 1] : 0;
+    const int mine = re - rb > lane ? (re - rb - lane + LPR - 1) / LPR : 0;  // this lane's entries
+    const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)mine);
+    const int k0 = rb + lane;
     XT s = XT(0);
-    for (int k0 = rb + lane; k0 < re; k0 += 4 * LPR) {
-      int c[4];
-      VT a[4];
-      XT xv[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int k = k0 + t * LPR;
-        c[t] = (k < re) ? __ldcs(ci + k) : -1;
-        a[t] = (k < re) ? __ldcs(v + k) : VT(0);
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        xv[t] = XT(0);
-        if (c[t] >= 0) {
-          if (PROLONG && c[t] < nrows) {
-            const int src = w[c[t]];
-            xv[t] = src >= 0 ? x[nrows + src] : XT(0);
-          } else {
-            xv[t] = __ldg(x + c[t]);
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (c[t] >= 0) s = vfma<VT, XT>(a[t], xv[t], s);
-    }
+    int j0 = 0;
+    for (; j0 + kVecBatch <= wmax; j0 += kVecBatch)
+      s = row_entries<VT, XT, PROLONG, kVecBatch, LPR>(ci, v, k0 + j0 * LPR, re, x, nrows, w, s, pol);
+    s = entries_tail<VT, XT, PROLONG, kVecBatch, LPR>(wmax - j0, ci, v, k0 + j0 * LPR, re, x, nrows, w, s, pol);
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LPR);
-    if (act && lane == 0) {
-      XT out;
-      if (MODE == SPMV_SET) out = s;
-      else if (MODE == SPMV_RESID) out = b[row] - s;
-      else if (MODE == SPMV_ADD) out = y[row] + s;
-      else if (MODE == SPMV_AXPB) out = coef[0] * b[row] + s;
-      else out = b[row] + s;
-      y[row] = out;
-      if (PROLONG) {
-        const int src = w[row];
-        xf[row] = src >= 0 ? x[nrows + src] : XT(0);
-      }
+    if (own) {
+      y[row] = row_output<MODE>(pre, s, coef);
+      if (PROLONG) xf[row] = pro;
     }
   }
 }
 
 template <typename VT, typename XT, int RB>
 static void launch_spmv_row(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y,
-                            int mode, const int* w, XT* xf, cudaStream_t s, const XT* coef) {
+                            int mode, const int* w, XT* xf, cudaStream_t s, const XT* coef, bool keep) {
   const int g1 = ceil_div(nrows, 256);
   if (w) {
-    airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr);
+    airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, true, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr, keep);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_AXPB: airg::note_launch(), k_spmv_row<VT, XT, SPMV_AXPB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_SET: airg::note_launch(), k_spmv_row<VT, XT, SPMV_SET, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_row<VT, XT, SPMV_RESID, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADD, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_AXPB: airg::note_launch(), k_spmv_row<VT, XT, SPMV_AXPB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    default: airg::note_launch(), k_spmv_row<VT, XT, SPMV_ADDB, false, RB><<<g1, 256, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
   }
 }
 
 template <typename VT, typename XT, int LPR>
 static void launch_spmv(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                        const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef) {
+                        const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef, bool keep) {
   if constexpr (LPR == 1) {
-    if (rb == 8) launch_spmv_row<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef);
-    else launch_spmv_row<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef);
+    if (rb == 8) launch_spmv_row<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef, keep);
+    else launch_spmv_row<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, coef, keep);
     return;
   }
   const int grid = ceil_div(nrows, kSpmvThreads / LPR);
   if (w) {
-    airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr);
+    airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, true><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, w, xf, nullptr, keep);
     return;
   }
   switch (mode) {
-    case SPMV_SET: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_RESID: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_ADD: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    case SPMV_AXPB: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_AXPB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
-    default: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef); break;
+    case SPMV_SET: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_SET, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_RESID: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_RESID, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_ADD: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADD, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    case SPMV_AXPB: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_AXPB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
+    default: airg::note_launch(), k_spmv_vec<VT, XT, LPR, SPMV_ADDB, false><<<grid, kSpmvThreads, 0, s>>>(nrows, rp, ci, v, x, b, y, nullptr, nullptr, coef, keep); break;
   }
 }
 
 template <typename VT, typename XT>
 static void spmv_dispatch(int nrows, const int* rp, const int* ci, const VT* v, const XT* x, const XT* b, XT* y, int mode,
-                          int lanes, const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef = nullptr) {
+                          int lanes, const int* w, XT* xf, cudaStream_t s, int rb, const XT* coef, bool keep) {
   switch (lanes) {
-    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
-    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
-    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
-    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
-    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
-    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef); break;
+    case 1: launch_spmv<VT, XT, 1>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
+    case 2: launch_spmv<VT, XT, 2>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
+    case 4: launch_spmv<VT, XT, 4>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
+    case 8: launch_spmv<VT, XT, 8>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
+    case 16: launch_spmv<VT, XT, 16>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
+    default: launch_spmv<VT, XT, 32>(nrows, rp, ci, v, x, b, y, mode, w, xf, s, rb, coef, keep); break;
   }
+}
+
+double l2_keep_bytes() {
+  static const double kb = [] {
+    const char* e = getenv("AIRG_L2_KEEP_MB");
+    return (e ? atof(e) : (double)kL2KeepMB) * 1048576.0;
+  }();
+  return kb;
+}
+template <typename VT>
+static bool keep_in_l2(const DCsr& A) {
+  return (double)A.nnz * (4.0 + sizeof(VT)) + 4.0 * (A.nrows + 1.0) <= l2_keep_bytes();
 }
 
 // Entries loaded per batch by the row-per-thread SpMV: 8 unless the rows average about 4 or fewer.
@@ -542,7 +573,7 @@ int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double*
   if (A.nrows <= 0) return AIRG_OK;
   if (A.sell) return sell_spmv(*A.sell, x, b, y, SPMV_AXPB, nullptr, nullptr, coef, s);
   spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, SPMV_AXPB, lanes, nullptr, nullptr, s, row_batch(A),
-                                coef);
+                                coef, keep_in_l2<double>(A));
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -550,7 +581,8 @@ int dev_spmv_axpb(const DCsr& A, const double* x, const double* b, const double*
 int dev_spmv(const DCsr& A, const double* x, const double* b, double* y, int mode, int lanes, cudaStream_t s) {
   if (A.nrows <= 0) return AIRG_OK;
   if (A.sell) return sell_spmv(*A.sell, x, b, y, mode, nullptr, nullptr, nullptr, s);
-  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s, row_batch(A));
+  spmv_dispatch<double, double>(A.nrows, A.rp, A.ci, A.v, x, b, y, mode, lanes, nullptr, nullptr, s, row_batch(A),
+                                nullptr, keep_in_l2<double>(A));
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -560,7 +592,8 @@ int dev_spmv_resid_prolong(const DCsr& AF, double* x, const int* w, const double
                            cudaStream_t s) {
   if (AF.nrows <= 0) return AIRG_OK;
   if (AF.sell) return sell_spmv(*AF.sell, x, b, y, SPMV_RESID, w, x, nullptr, s);
-  spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s, row_batch(AF));
+  spmv_dispatch<double, double>(AF.nrows, AF.rp, AF.ci, AF.v, x, b, y, SPMV_RESID, lanes, w, x, s, row_batch(AF),
+                                nullptr, keep_in_l2<double>(AF));
   KERNEL_CHECK();
   return AIRG_OK;
 }
@@ -574,9 +607,10 @@ int dev_spmv_lo(const DCsr& A, const void* vals, int vt, const float* x, const f
   if (A.sell && A.sell->v_lo && A.sell->vt == vt) return sell_spmv_lo(*A.sell, x, b, y, mode, w, xf, s);
   if (vt == 2)
     spmv_dispatch<__nv_bfloat16, float>(A.nrows, A.rp, A.ci, (const __nv_bfloat16*)vals, x, b, y, mode, lanes, w, xf, s,
-                                        row_batch(A));
+                                        row_batch(A), nullptr, keep_in_l2<__nv_bfloat16>(A));
   else
-    spmv_dispatch<float, float>(A.nrows, A.rp, A.ci, (const float*)vals, x, b, y, mode, lanes, w, xf, s, row_batch(A));
+    spmv_dispatch<float, float>(A.nrows, A.rp, A.ci, (const float*)vals, x, b, y, mode, lanes, w, xf, s, row_batch(A),
+                                nullptr, keep_in_l2<float>(A));
   KERNEL_CHECK();
   return AIRG_OK;
 }

@@ -33,14 +33,14 @@ __device__ __forceinline__ float sfma(__nv_bfloat16 a, float x, float acc) { ret
 
 template <int R, bool PROLONG, typename VT, typename XT>
 __device__ __forceinline__ XT sell_batch(const int* cs, const VT* vs, int k0, const XT* x, int nrows,
-                                         const int* __restrict__ w, XT s) {
+                                         const int* __restrict__ w, XT s, uint64_t pol) {
   int c[R];
   VT a[R];
   XT xv[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    c[t] = __ldcs(cs + (k0 + t) * 32);
-    a[t] = __ldcs(vs + (k0 + t) * 32);
+    c[t] = ld_pol(cs + (k0 + t) * 32, pol);
+    a[t] = ld_pol(vs + (k0 + t) * 32, pol);
   }
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
                                                    const int* __restrict__ ci, const VT* __restrict__ v,
                                                    const int* __restrict__ perm, const XT* x, const XT* b,
                                                    XT* y, const int* __restrict__ w, XT* xf,
-                                                   const XT* __restrict__ coef) {
+                                                   const XT* __restrict__ coef, bool keep) {
+  const uint64_t pol = l2_policy(keep);
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long sl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices; sl += nwarps) {
@@ -81,15 +82,15 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
     const VT* vs = v + beg + lane;
     XT s = XT(0);
     int k0 = 0;
-    for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s);
+    for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s, pol);
     switch (width - k0) {  // warp-uniform remainder
-      case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 4: s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 5: s = sell_batch<5, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 6: s = sell_batch<6, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
-      case 7: s = sell_batch<7, PROLONG>(cs, vs, k0, x, nrows, w, s); break;
+      case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 4: s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 5: s = sell_batch<5, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 6: s = sell_batch<6, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+      case 7: s = sell_batch<7, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
       default: break;
     }
     if (row >= 0) {
@@ -188,8 +189,11 @@ template <int MODE, bool PROLONG, typename VT, typename XT>
 void launch_sell(const DSell& S, const VT* vals, const XT* x, const XT* b, XT* y, const int* w, XT* xf,
                  const XT* coef, cudaStream_t s) {
   const int grid = ceil_div(S.nslices, 256 / 32);
+  // the same size rule as the CSR SpMVs: the copy's padded arrays against the L2 keep size
+  const bool keep = (double)S.nnz_pad * (4.0 + sizeof(VT)) + 4.0 * (S.nslices + 1.0) + 4.0 * 32.0 * S.nslices <=
+                    l2_keep_bytes();
   airg::note_launch(), k_spmv_sell<MODE, PROLONG, VT, XT><<<grid, 256, 0, s>>>(S.nslices, S.nrows, S.sp, S.ci, vals,
-                                                                               S.perm, x, b, y, w, xf, coef);
+                                                                               S.perm, x, b, y, w, xf, coef, keep);
 }
 
 template <typename VT, typename XT>
