@@ -2218,35 +2218,71 @@ int build_level(const DCsr& A, const SetupParams& p, int level, bool force_coars
 // ------------------------------------------------------------------------------------------
 // Solve-phase operators in the F-then-C numbering
 // ------------------------------------------------------------------------------------------
-__global__ void k_af_fill(int nf, DCsr Aff, DCsr Afc, const int* __restrict__ pos_next, DCsr AF) {
-  for (long long ff = (long long)blockIdx.x * blockDim.x + threadIdx.x; ff < nf; ff += (long long)gridDim.x * blockDim.x) {
-    const int f = (int)ff;
-    int o = Aff.rp[f] + Afc.rp[f];
-    AF.rp[f] = o;
-    if (f == nf - 1) AF.rp[nf] = Aff.rp[nf] + Afc.rp[nf];
-    for (int k = Aff.rp[f]; k < Aff.rp[f + 1]; ++k) { AF.ci[o] = Aff.ci[k]; AF.v[o++] = Aff.v[k]; }
-    for (int k = Afc.rp[f]; k < Afc.rp[f + 1]; ++k) {
-      const int c = Afc.ci[k];
-      AF.ci[o] = nf + (pos_next ? pos_next[c] : c);
-      AF.v[o++] = Afc.v[k];
-    }
+// Last row of the block's window [0, nr) whose start is <= p (empty rows share their successor's
+// start, so the row found is the one that holds entry p).
+__device__ __forceinline__ int window_row(const int* srp, int nr, int p) {
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (srp[mid] <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// AF row f = A_ff row f, then A_fc row f with columns nf + pos_next[c].  Entry-parallel: a block
+// takes 256 rows, stages both row-pointer windows in shared memory, and each thread moves single
+// entries (an A_ff entry p of row f goes to p + Afc.rp[f], an A_fc entry to p + Aff.rp[f + 1]), so
+// loads and stores are coalesced instead of each thread walking its own short row.
+__global__ void __launch_bounds__(256) k_af_fill(int nf, DCsr Aff, DCsr Afc, const int* __restrict__ pos_next, DCsr AF) {
+  __shared__ int sff[257], sfc[257];
+  const int r0 = blockIdx.x * 256;
+  const int nr = min(256, nf - r0);
+  for (int t = threadIdx.x; t <= nr; t += 256) {
+    sff[t] = Aff.rp[r0 + t];
+    sfc[t] = Afc.rp[r0 + t];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nr) AF.rp[r0 + threadIdx.x] = sff[threadIdx.x] + sfc[threadIdx.x];
+  if (threadIdx.x == 0 && r0 + nr == nf) AF.rp[nf] = sff[nr] + sfc[nr];
+  for (int p = sff[0] + threadIdx.x; p < sff[nr]; p += 256) {
+    const int o = p + sfc[window_row(sff, nr, p)];
+    AF.ci[o] = Aff.ci[p];
+    AF.v[o] = Aff.v[p];
+  }
+  for (int p = sfc[0] + threadIdx.x; p < sfc[nr]; p += 256) {
+    const int o = p + sff[window_row(sfc, nr, p) + 1];
+    const int c = Afc.ci[p];
+    AF.ci[o] = nf + (pos_next ? pos_next[c] : c);
+    AF.v[o] = Afc.v[p];
   }
 }
 __global__ void k_perm_rows_count(int n, const int* __restrict__ rp, const int* __restrict__ pos, int* __restrict__ cnt) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     cnt[pos ? pos[i] : i] = rp[i + 1] - rp[i];
 }
-// row pos[i] of out <- row i of A; columns mapped by cpos (nullptr: kept) plus coff
-__global__ void k_perm_rows_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
-                                 const int* __restrict__ pos, const int* __restrict__ cpos, const int* __restrict__ orp,
-                                 int* __restrict__ oci, double* __restrict__ ov) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    int o = orp[pos ? pos[i] : i];
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      const int j = ci[k];
-      oci[o] = cpos ? cpos[j] : j;
-      ov[o++] = v[k];
-    }
+// row pos[i] of out <- row i of A; columns mapped by cpos (nullptr: kept).  Entry-parallel over the
+// source rows (a block takes 256 of them with their source and destination row starts in shared
+// memory), so the reads are coalesced and each row's writes stay contiguous.
+__global__ void __launch_bounds__(256) k_perm_rows_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                        const double* __restrict__ v, const int* __restrict__ pos,
+                                                        const int* __restrict__ cpos, const int* __restrict__ orp,
+                                                        int* __restrict__ oci, double* __restrict__ ov) {
+  __shared__ int srp[257], sdst[256];
+  const int r0 = blockIdx.x * 256;
+  const int nr = min(256, n - r0);
+  for (int t = threadIdx.x; t <= nr; t += 256) srp[t] = rp[r0 + t];
+  if ((int)threadIdx.x < nr) {
+    const int i = r0 + threadIdx.x;
+    sdst[threadIdx.x] = orp[pos ? pos[i] : i];
+  }
+  __syncthreads();
+  for (int p = srp[0] + threadIdx.x; p < srp[nr]; p += 256) {
+    const int lo = window_row(srp, nr, p);
+    const int o = sdst[lo] + (p - srp[lo]);
+    const int j = ci[p];
+    oci[o] = cpos ? cpos[j] : j;
+    ov[o] = v[p];
   }
 }
 __global__ void k_w_solve(int nf, const int* __restrict__ w, const int* __restrict__ pos_next, int* __restrict__ ws) {
@@ -2276,14 +2312,16 @@ int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs
                     Arena& tmp, cudaStream_t s) {
   const int nf = L.nf, nc = L.nc;
   AIRG_TRY(own.csr(AF, nf, nf + nc, L.Aff.nnz + L.Afc.nnz));
-  if (nf > 0) airg::note_launch(), k_af_fill<<<GRID(nf)>>>(nf, L.Aff, L.Afc, pos_next, AF);
+  if (nf > 0) airg::note_launch(), k_af_fill<<<ceil_div(nf, 256), 256, 0, s>>>(nf, L.Aff, L.Afc, pos_next, AF);
   KERNEL_CHECK();
   AIRG_TRY(own.csr(Zs, nc, nf, L.Z.nnz));
   int* cnt;
   AIRG_TRY(tmp.alloc(&cnt, std::max(nc, 1)));
   if (nc > 0) airg::note_launch(), k_perm_rows_count<<<GRID(nc)>>>(nc, L.Z.rp, pos_next, cnt);
   AIRG_TRY(scan_i32(cnt, Zs.rp, nc, tmp, s, nullptr));
-  if (nc > 0) airg::note_launch(), k_perm_rows_fill<<<GRID(nc)>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, pos_next, nullptr, Zs.rp, Zs.ci, Zs.v);
+  if (nc > 0)
+    airg::note_launch(), k_perm_rows_fill<<<ceil_div(nc, 256), 256, 0, s>>>(nc, L.Z.rp, L.Z.ci, L.Z.v, pos_next, nullptr,
+                                                                           Zs.rp, Zs.ci, Zs.v);
   AIRG_TRY(own.alloc(ws, std::max(nf, 1)));
   if (nf > 0) airg::note_launch(), k_w_solve<<<GRID(nf)>>>(nf, L.w, pos_next, *ws);
   KERNEL_CHECK();
@@ -2294,7 +2332,8 @@ int build_solve_ops(const LevelBuild& L, const int* pos_next, DCsr& AF, DCsr& Zs
     AIRG_TRY(tmp.alloc(&wcnt, std::max(nf, 1)));
     airg::note_launch(), k_perm_rows_count<<<GRID(nf)>>>(nf, L.W.rp, nullptr, wcnt);
     AIRG_TRY(scan_i32(wcnt, Ws.rp, nf, tmp, s, nullptr));
-    airg::note_launch(), k_perm_rows_fill<<<GRID(nf)>>>(nf, L.W.rp, L.W.ci, L.W.v, nullptr, pos_next, Ws.rp, Ws.ci, Ws.v);
+    airg::note_launch(), k_perm_rows_fill<<<ceil_div(nf, 256), 256, 0, s>>>(nf, L.W.rp, L.W.ci, L.W.v, nullptr, pos_next,
+                                                                           Ws.rp, Ws.ci, Ws.v);
     KERNEL_CHECK();
   }
   return AIRG_OK;
@@ -2307,7 +2346,9 @@ int permute_matrix(const DCsr& A, const int* pos, DCsr& out, Arena& own, Arena& 
   AIRG_TRY(tmp.alloc(&cnt, std::max(n, 1)));
   if (n > 0) airg::note_launch(), k_perm_rows_count<<<GRID(n)>>>(n, A.rp, pos, cnt);
   AIRG_TRY(scan_i32(cnt, out.rp, n, tmp, s, nullptr));
-  if (n > 0) airg::note_launch(), k_perm_rows_fill<<<GRID(n)>>>(n, A.rp, A.ci, A.v, pos, pos, out.rp, out.ci, out.v);
+  if (n > 0)
+    airg::note_launch(), k_perm_rows_fill<<<ceil_div(n, 256), 256, 0, s>>>(n, A.rp, A.ci, A.v, pos, pos, out.rp, out.ci,
+                                                                          out.v);
   KERNEL_CHECK();
   return AIRG_OK;
 }
