@@ -85,7 +85,7 @@ def job_value(dofs_per_rank: int, steps: int, world: int, seconds: float) -> flo
 # top-level SpMV kernels: (ncu summary, source file, the kernel's signature start)
 SPMV_KERNELS = {
     "k_spmv_sell": ("k_spmv_sell_top_level_2d_p1dg_640.md", "airg_sell.cu",
-                    "__global__ void __launch_bounds__(256) k_spmv_sell("),
+                    "__global__ void __launch_bounds__(256, PROLONG ? 6 : 8) k_spmv_sell("),
     "k_spmv_row": ("k_spmv_row_top_level_2d_p1dg_640.md", "airg_prims.cu",
                    "__global__ void __launch_bounds__(256) k_spmv_row("),
 }

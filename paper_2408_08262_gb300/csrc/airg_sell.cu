@@ -65,8 +65,10 @@ __device__ __forceinline__ XT sell_batch(const int* cs, const VT* vs, int k0, co
 // prefetched the next slice's offsets measured 40 % slower), lane l of slice s computes row
 // perm[32 s + l].
 // ------------------------------------------------------------------------------------------
+// Eight resident CTAs per SM (32 registers) with 8-entry batches; the fused-prolongation variant,
+// whose gathers hold more registers, takes 4-entry batches at six CTAs (40 registers).
 template <int MODE, bool PROLONG, typename VT = double, typename XT = double>
-__global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const int* __restrict__ sp,
+__global__ void __launch_bounds__(256, PROLONG ? 6 : 8) k_spmv_sell(int nslices, int nrows, const int* __restrict__ sp,
                                                    const int* __restrict__ ci, const VT* __restrict__ v,
                                                    const int* __restrict__ perm, const XT* x, const XT* b,
                                                    XT* y, const int* __restrict__ w, XT* xf,
@@ -82,16 +84,26 @@ __global__ void __launch_bounds__(256) k_spmv_sell(int nslices, int nrows, const
     const VT* vs = v + beg + lane;
     XT s = XT(0);
     int k0 = 0;
-    for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s, pol);
-    switch (width - k0) {  // warp-uniform remainder
-      case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 4: s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 5: s = sell_batch<5, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 6: s = sell_batch<6, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      case 7: s = sell_batch<7, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
-      default: break;
+    if constexpr (PROLONG) {
+      for (; k0 + 4 <= width; k0 += 4) s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s, pol);
+      switch (width - k0) {  // warp-uniform remainder
+        case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        default: break;
+      }
+    } else {
+      for (; k0 + 8 <= width; k0 += 8) s = sell_batch<8, PROLONG>(cs, vs, k0, x, nrows, w, s, pol);
+      switch (width - k0) {  // warp-uniform remainder
+        case 1: s = sell_batch<1, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 2: s = sell_batch<2, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 3: s = sell_batch<3, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 4: s = sell_batch<4, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 5: s = sell_batch<5, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 6: s = sell_batch<6, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        case 7: s = sell_batch<7, PROLONG>(cs, vs, k0, x, nrows, w, s, pol); break;
+        default: break;
+      }
     }
     if (row >= 0) {
       XT out;
