@@ -1318,6 +1318,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
                                                             int* n_next, int lim) {
   __shared__ int hkey[WARPS][CAP];
   __shared__ double hval[WARPS][CAP];
+  __shared__ double s_a[WARPS][32];
+  __shared__ int s_b0[WARPS][32], s_len[WARPS][32];
   const int nrows = *nrows_dev;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int* key = hkey[wid];
@@ -1335,25 +1337,56 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int
     while (H < ub) { H <<= 1; ++lg; }
     for (int t = lane; t < H; t += 32) { key[t] = -1; val[t] = 0.0; }
     __syncwarp();
-    const int ab = g.arp[i], ae = g.arp[i + 1];
-    for (int k = ab; k < ae; ++k) {
-      const int l = g.aci[k];
-      const double a = g.av[k];
-      int b0, b1;
-      spg_brow(g, l, b0, b1);
-      const int len = b1 - b0;
-      for (int t = lane; t < len; t += 32) {
-        const int j = g.bci[b0 + t];
-        const double bv = g.bv[b0 + t];
-        unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - lg);
-        while (true) {
-          const int prev = atomicCAS(&key[h], -1, j);
-          if (prev == -1 || prev == j) break;
-          h = (h + 1) & (H - 1);
-        }
-        val[h] = fma(a, bv, val[h]);
+    // A entries 32 at a time: their values and B row ranges are loaded by the lanes together and
+    // kept in shared memory, and the first 32 candidates of the next entry are loaded while the
+    // current entry's slots are updated, so the entries do not each wait on a chain of dependent
+    // global loads.  The updates themselves stay one entry after another, in ascending order.
+    const int ab = g.arp[i], na = g.arp[i + 1] - ab;
+    double* sa = s_a[wid];
+    int* sb0 = s_b0[wid];
+    int* slen = s_len[wid];
+    for (int e0 = 0; e0 < na; e0 += 32) {
+      const int ne = min(32, na - e0);
+      if (lane < ne) {
+        const int l = g.aci[ab + e0 + lane];
+        sa[lane] = g.av[ab + e0 + lane];
+        int b0, b1;
+        spg_brow(g, l, b0, b1);
+        sb0[lane] = b0;
+        slen[lane] = b1 - b0;
       }
       __syncwarp();
+      int jn = -1;
+      double bn = 0.0;
+      if (lane < slen[0]) {
+        jn = g.bci[sb0[0] + lane];
+        bn = g.bv[sb0[0] + lane];
+      }
+      for (int e = 0; e < ne; ++e) {
+        const double a = sa[e];
+        const int b0 = sb0[e], len = slen[e];
+        const int j0 = jn;
+        const double bv0 = bn;
+        if (e + 1 < ne) {  // next entry's first candidates
+          jn = -1;
+          if (lane < slen[e + 1]) {
+            jn = g.bci[sb0[e + 1] + lane];
+            bn = g.bv[sb0[e + 1] + lane];
+          }
+        }
+        for (int t = lane; t < len; t += 32) {
+          const int j = t < 32 ? j0 : g.bci[b0 + t];
+          const double bv = t < 32 ? bv0 : g.bv[b0 + t];
+          unsigned h = ((unsigned)j * 0x9E3779B1u) >> (32 - lg);
+          while (true) {
+            const int prev = atomicCAS(&key[h], -1, j);
+            if (prev == -1 || prev == j) break;
+            h = (h + 1) & (H - 1);
+          }
+          val[h] = fma(a, bv, val[h]);
+        }
+        __syncwarp();
+      }
     }
     // compact occupied slots to the front (chunks read before written), then sort by column
     int u = 0;
