@@ -1313,7 +1313,7 @@ __device__ __forceinline__ int spg_rank_write(const SpgArgs& g, int* key, const 
 }
 
 template <int CAP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SpgArgs g, const int* __restrict__ rows,
+__global__ void __launch_bounds__(WARPS * 32, CAP <= 512 ? 4 : 1) k_spgemm_warp(SpgArgs g, const int* __restrict__ rows,
                                                             const int* __restrict__ nrows_dev, int* next_rows,
                                                             int* n_next, int lim) {
   __shared__ int hkey[WARPS][CAP];
@@ -1928,10 +1928,11 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
   AIRG_TRY(tmp.alloc(&g.tcol, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.tval, (size_t)std::max(total, 1LL)));
   AIRG_TRY(tmp.alloc(&g.cnt, std::max(ar, 1)));
-  // row lists of the wider paths; counters: [0] mid, [1] big, [2] long, [3] error, [6] longest,
-  // [7] rows past the first expand-sort tier
-  int *mid, *big, *lng, *rest, *rest2, *ctr;
+  // row lists of the wider paths; counters: [0] mid, [1] big, [2] long, [3] error, [5] rows past
+  // the 512-slot tier, [6] longest, [7] rows past the first expand-sort tier
+  int *mid, *big, *big2, *lng, *rest, *rest2, *ctr;
   AIRG_TRY(tmp.alloc(&rest2, std::max(ar, 1)));
+  AIRG_TRY(tmp.alloc(&big2, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&mid, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&big, std::max(ar, 1)));
   AIRG_TRY(tmp.alloc(&lng, std::max(ar, 1)));
@@ -1943,7 +1944,10 @@ int spgemm_padded(const DCsr& A, const DCsr* Bc, const SpgPadded* Bp, double sca
     AIRG_TRY(spgemm_smem_attributes());
     const size_t stage_smem = sizeof(WarpStage) * kStageWarps;
     airg::note_launch(), k_spgemm_warp_staged<<<152 * 3, kStageWarps * 32, stage_smem, s>>>(g, mid, ctr + 0, big, ctr + 1);
-    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big, ctr + 1, lng, ctr + 2, kWarpCap);
+    // rows of at most 512 candidates: a 512-slot table, eight warps per CTA and four CTAs per SM
+    // (twice the warps of the 1024-slot tier)
+    airg::note_launch(), k_spgemm_warp<512, 8><<<152 * 4, 8 * 32, 0, s>>>(g, big, ctr + 1, big2, ctr + 5, 512);
+    airg::note_launch(), k_spgemm_warp<kWarpCap, 4><<<152 * 4, 4 * 32, 0, s>>>(g, big2, ctr + 5, lng, ctr + 2, kWarpCap);
     // rows of 1025-2048 candidates: the hash warp kernel with a 2048-slot table (two warps per
     // CTA); 2049-4096: expand-sort-compress; beyond: the per-column block kernel.
     // AIRG_SPGEMM_NO_ESC=1 sends every row above 1024 candidates to the block kernel (same results)
