@@ -174,19 +174,22 @@ __global__ void __launch_bounds__(256) k_seg_gs(const double* __restrict__ V, lo
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  // NC == ncols (one instance per column count): no FP64 instruction is issued for an absent
+  // column -- sm_103a's FP64 pipe spends a warp instruction's time on predicated-off lanes too
+  const bool want = nd > 0;
   for (long long r = t.lo[b] + threadIdx.x; r < t.hi[b]; r += blockDim.x) {
     double wr = w[r];
     if (hsub) {
       double sub = 0.0;
 #pragma unroll
-      for (int k = 0; k < NC; ++k)
-        if (k < ncols) sub += V[(size_t)k * ldv + r] * sh[k];
+      for (int k = 0; k < NC; ++k) sub += V[(size_t)k * ldv + r] * sh[k];
       wr -= sub;
       w[r] = wr;
     }
+    if (want) {
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
-      if (k < nd) acc[k] += V[(size_t)k * ldv + r] * wr;
+      for (int k = 0; k < NC; ++k) acc[k] += V[(size_t)k * ldv + r] * wr;
+    }
     acc[NC] += wr * wr;
   }
 #pragma unroll
@@ -549,10 +552,21 @@ int batch_graph(airg_batch* B) {
 int seg_gs(airg_batch* B, const double* V, int ncols, double* w, const double* hsub, double* dots, double* nrm) {
   const SegTab& t = B->seg;
   const long long ld = B->N;
-  if (ncols <= 4) airg::note_launch(), k_seg_gs<4><<<t.nblk, 256, 0, B->s>>>(V, ld, ncols, w, t, hsub, dots, nrm);
-  else if (ncols <= 8) airg::note_launch(), k_seg_gs<8><<<t.nblk, 256, 0, B->s>>>(V, ld, ncols, w, t, hsub, dots, nrm);
-  else if (ncols <= 16) airg::note_launch(), k_seg_gs<16><<<t.nblk, 256, 0, B->s>>>(V, ld, ncols, w, t, hsub, dots, nrm);
-  else airg::note_launch(), k_seg_gs<32><<<t.nblk, 256, 0, B->s>>>(V, ld, ncols, w, t, hsub, dots, nrm);
+  if (ncols == 0 && hsub) return AIRG_ERR_ARG;
+  switch (ncols) {
+    case 0:  // the norm alone (no columns to subtract or project on)
+      airg::note_launch(), k_seg_gs<1><<<t.nblk, 256, 0, B->s>>>(V, ld, 0, w, t, nullptr, dots, nrm);
+      break;
+#define AIRG_SEG_GS(N) \
+  case N: airg::note_launch(), k_seg_gs<N><<<t.nblk, 256, 0, B->s>>>(V, ld, ncols, w, t, hsub, dots, nrm); break;
+    AIRG_SEG_GS(1) AIRG_SEG_GS(2) AIRG_SEG_GS(3) AIRG_SEG_GS(4) AIRG_SEG_GS(5) AIRG_SEG_GS(6) AIRG_SEG_GS(7)
+    AIRG_SEG_GS(8) AIRG_SEG_GS(9) AIRG_SEG_GS(10) AIRG_SEG_GS(11) AIRG_SEG_GS(12) AIRG_SEG_GS(13) AIRG_SEG_GS(14)
+    AIRG_SEG_GS(15) AIRG_SEG_GS(16) AIRG_SEG_GS(17) AIRG_SEG_GS(18) AIRG_SEG_GS(19) AIRG_SEG_GS(20) AIRG_SEG_GS(21)
+    AIRG_SEG_GS(22) AIRG_SEG_GS(23) AIRG_SEG_GS(24) AIRG_SEG_GS(25) AIRG_SEG_GS(26) AIRG_SEG_GS(27) AIRG_SEG_GS(28)
+    AIRG_SEG_GS(29) AIRG_SEG_GS(30) AIRG_SEG_GS(31) AIRG_SEG_GS(32)
+#undef AIRG_SEG_GS
+    default: return AIRG_ERR_ARG;
+  }
   KERNEL_CHECK();
   return AIRG_OK;
 }
