@@ -1580,14 +1580,35 @@ __global__ void __launch_bounds__(kStageWarps * 32) k_spgemm_warp_staged(SpgArgs
     for (int s2 = 16; s2 > 0; s2 >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, s2));
     const long long thr = spg_thr(g, mx);
     const long long o = g.ubo[i];
-    // order by rank: a kept entry's output position is the number of kept columns below it;
-    // dropped entries take the key 0x7fffffff, which is below no kept column
-    int kept;
-    if (u <= 32) kept = spg_rank_write<1>(g, key, val, u, thr, i, o, lane);
-    else if (u <= 64) kept = spg_rank_write<2>(g, key, val, u, thr, i, o, lane);
-    else if (u <= 128) kept = spg_rank_write<4>(g, key, val, u, thr, i, o, lane);
-    else kept = spg_rank_write<8>(g, key, val, u, thr, i, o, lane);
-    if (lane == 0) g.cnt[i] = kept;
+    // drop first (the threshold is known), so that only the kept entries are ranked: the ranking
+    // costs each lane one pass over the entries per NE of its own
+    int u2 = 0;
+    for (int base = 0; base < u; base += 32) {
+      const int t = base + lane;
+      int j = 0;
+      double c = 0.0;
+      bool keep = false;
+      if (t < u) {
+        j = key[t];
+        c = val[t];
+        keep = abs_bits(c) >= thr || (g.keep_diag && j == i);
+      }
+      const unsigned bal = __ballot_sync(FULL, keep);
+      __syncwarp();
+      if (keep) {
+        const int d = u2 + __popc(bal & ((1u << lane) - 1u));
+        key[d] = j;
+        val[d] = c;
+      }
+      u2 += __popc(bal);
+      __syncwarp();
+    }
+    // order by rank among the kept columns (threshold 0: every entry left is kept)
+    if (u2 <= 32) spg_rank_write<1>(g, key, val, u2, 0, i, o, lane);
+    else if (u2 <= 64) spg_rank_write<2>(g, key, val, u2, 0, i, o, lane);
+    else if (u2 <= 128) spg_rank_write<4>(g, key, val, u2, 0, i, o, lane);
+    else spg_rank_write<8>(g, key, val, u2, 0, i, o, lane);
+    if (lane == 0) g.cnt[i] = u2;
     __syncwarp();
   }
 }
