@@ -708,15 +708,17 @@ __device__ __forceinline__ void house_warp(double (&M)[RPL][C], int lane) {
     const double vn2 = 2.0 * xn * (xn + fabs(x0));
     if (vn2 > 0.0) {
       const double two_over = 2.0 / vn2;
+      // v = x - a e_k: lane k's first-row entry of v is x0 - a, the rest are x's own entries; one
+      // FMA per row with the operand selected (an FP64 instruction costs its full pipe time on
+      // sm_103a however many lanes it has)
+      const double v0 = (lane == k) ? x0 - a : M[0][k];
 #pragma unroll
       for (int j = k + 1; j < C; ++j) {
         const double mkj = __shfl_sync(FULL, M[0][j], k);
         const double f = (p[j] - a * mkj) * two_over;
+        if (lane >= k) M[0][j] = fma(-f, v0, M[0][j]);
 #pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          if (q > 0 || lane > k) M[q][j] = fma(-f, M[q][k], M[q][j]);
-          else if (lane == k) M[q][j] = fma(-f, x0 - a, M[q][j]);
-        }
+        for (int q = 1; q < RPL; ++q) M[q][j] = fma(-f, M[q][k], M[q][j]);
       }
     }
     if (lane == k) M[0][k] = a;
@@ -857,8 +859,14 @@ int tsqr_run(const double* K, long long n, int nc, int m, double* alpha, int* fi
   AIRG_TRY(tmp.alloc(&fbuf, (size_t)ftot));
   AIRG_TRY(tmp.alloc(&cnt, (size_t)std::max(1LL, ctot)));
   if (ctot > 0) CU_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)ctot, s));
-  const long long blocks = (plan.ntiles[0] + 7) / 8;
-  airg::note_launch(), k_tsqr<C, RPL, RPLC><<<(unsigned)blocks, 256, 0, s>>>(K, n, nc, plan, fbuf, cnt, m, alpha, fitted);
+  // The tiles are independent warps.  The 8- and 4-row instances hold 98-186 registers a thread,
+  // where a 256-thread CTA leaves an SM with 8 warps and single-warp CTAs fit 10-11 (and end in a
+  // finer tail: 20 % faster on the largest levels); the 2-row instances (58-128 registers) gain no
+  // warps from it and lose time to the extra CTA launches, so they keep 8 warps a CTA.
+  constexpr int warps = RPL >= 4 ? 1 : 8;
+  const long long blocks = (plan.ntiles[0] + warps - 1) / warps;
+  if (blocks > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
+  airg::note_launch(), k_tsqr<C, RPL, RPLC><<<(unsigned)blocks, 32 * warps, 0, s>>>(K, n, nc, plan, fbuf, cnt, m, alpha, fitted);
   return cuda_status(cudaGetLastError());
 }
 
