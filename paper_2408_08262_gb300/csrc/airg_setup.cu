@@ -859,10 +859,13 @@ int tsqr_run(const double* K, long long n, int nc, int m, double* alpha, int* fi
   AIRG_TRY(tmp.alloc(&fbuf, (size_t)ftot));
   AIRG_TRY(tmp.alloc(&cnt, (size_t)std::max(1LL, ctot)));
   if (ctot > 0) CU_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)ctot, s));
-  // The tiles are independent warps.  The 8- and 4-row instances hold 98-186 registers a thread,
-  // where a 256-thread CTA leaves an SM with 8 warps and single-warp CTAs fit 10-11 (and end in a
-  // finer tail: 20 % faster on the largest levels); the 2-row instances (58-128 registers) gain no
-  // warps from it and lose time to the extra CTA launches, so they keep 8 warps a CTA.
+  // The tiles are independent warps.  In an 8-warp CTA the eight tiles of a combine group finish
+  // together and the last of them then combines the group alone, holding the CTA's slot with one
+  // warp busy; with single-warp CTAs the seven finished warps' slots take new tiles at once.  The
+  // resident warps are the same (registers come from each sub-partition's quarter of the file:
+  // two warps of 170 registers a sub-partition either way), but the FP64 pipe is busy 83 % instead
+  // of 68 % of the active cycles on the 8-row instance (20 % faster on the largest levels).  The
+  // 2-row instances lost time to the extra CTA launches, so they keep 8 warps a CTA.
   constexpr int warps = RPL >= 4 ? 1 : 8;
   const long long blocks = (plan.ntiles[0] + warps - 1) / warps;
   if (blocks > 0x7fffffffLL) return AIRG_ERR_UNSUPPORTED;
